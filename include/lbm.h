@@ -1,0 +1,160 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) decoupled Hermite-expansion lattice
+ * Boltzmann library (liblbm.so).
+ *
+ * The method is Hu, Zhang & Geng, "A decoupled scheme based on the Hermite
+ * expansion to construct lattice Boltzmann models for the compressible
+ * Navier-Stokes equations with arbitrary specific heat ratio" (arXiv
+ * 1606.06107).  Each lattice node carries
+ *   - Q_t translational populations g_i (the paper's g_i, Eq. DisEvolI) on a
+ *     4th-order Hermite lattice: D1Q7 (Table II used as a 1-D translational
+ *     set), D2Q37 (Table I) or the tensor product D2Q49 = D1Q7 x D1Q7, and
+ *   - Q_r = 7 rotational populations h_j (Eq. EvoEtaJ) on D1Q7 (Table II)
+ *     when the number of rotational degrees of freedom n > 0 (Q_r = 0 for
+ *     n = 0).  The specific-heat ratio is gamma = (D+n+2)/(D+n) (Sec. III).
+ *
+ * One step advances both populations: moments rho, u, T of the time-t
+ * populations (Sec. V steps 3-4, Eq. T), 4th-order Hermite equilibria
+ * (Sec. IV), BGK relaxation, and transport.  Two transport modes exist:
+ *   LBM_MODE_STREAM  g is pulled exactly on the lattice, g_i(x,t) =
+ *                    ft_i(x - e_i) with xi_i = r e_i and dt = dx/r (the time
+ *                    mapping t = step/(X r) of Sec. VI); the stored ft is the
+ *                    post-collision value; omega = 1/tau (tau in steps).
+ *   LBM_MODE_FD      the paper's forward-Euler + third-order upwind scheme
+ *                    for g (Eq. DisEvolSpaTiI) with dt = dx/(m r);
+ *                    omega = 1/(m tau).
+ * In both modes h is advected by the fluid velocity with the third-order
+ * upwind scheme of Eq. DisEvolSpaTiJ at Courant number u dt/dx and relaxed
+ * toward h^eq(T).
+ *
+ * Units are the paper's dimensionless ones (Eq. DDF, theta0 = 1): P = rho T.
+ *
+ * Population order: velocities sorted by (ez, ey, ex) ascending; for D1Q7
+ * index i has e = i - 3; for D2Q49 index i = (ey+3)*7 + (ex+3); for D2Q37
+ * the D2Q49 order with the 12 velocities |e| in {(2,2),(2,3),(3,2)}
+ * removed.  Rotational index j has eta_j = r (j - 3).
+ *
+ * Memory ownership: the library never allocates device memory.  The caller
+ * allocates two state buffers and one work buffer of the sizes reported by
+ * lbm_set_grid (any allocator; 256-byte alignment required) and binds them
+ * with lbm_bind.  The handle owns host memory only.
+ *
+ * Field layout for lbm_set_macro / lbm_get_moments: float32 device arrays,
+ * x fastest, unpadded, N = X*Y*Z entries; u is structure-of-arrays,
+ * u[a*N + node] for axis a < D.
+ *
+ * Errors: every call returns an lbm_status; lbm_last_error gives a message.
+ * Kernels never trap: a non-finite or non-positive rho or T found by a step
+ * sets a sticky device flag that lbm_status and lbm_conservation report as
+ * LBM_ENONFINITE.
+ *
+ * Threading: a handle is used by one host thread at a time.  Work is
+ * enqueued on the stream given to lbm_bind; calls documented as
+ * "synchronizing" wait for that stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx *lbm_handle;
+
+enum lbm_lattice { LBM_D1Q7 = 1, LBM_D2Q37 = 2, LBM_D2Q49 = 3, LBM_D3Q343 = 4 };
+enum lbm_bc { LBM_BC_PERIODIC = 0, LBM_BC_COPY = 1 };
+enum lbm_mode { LBM_MODE_STREAM = 0, LBM_MODE_FD = 1 };
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,     /* bad argument */
+    LBM_ESIZE = -2,      /* grid or buffer size out of range */
+    LBM_ECUDA = -3,      /* a CUDA runtime call failed */
+    LBM_ENONFINITE = -4, /* a step produced non-finite or non-positive rho/T */
+    LBM_ETIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+    LBM_ESTATE = -6      /* call out of order (e.g. step before bind) */
+};
+
+/* Create a solver.  D in {1,2,3}; lattice one of lbm_lattice with dimension
+ * D; n >= 0 rotational degrees of freedom (gamma = (D+n+2)/(D+n), Sec. III);
+ * tau > 0 relaxation time in lattice steps (Eq. DisEvolI/EvoEtaJ).  The
+ * lattice scaling factor r and weights (Tables I, II) are solved on the host
+ * in double precision from the Gauss-Hermite moment equations and rounded
+ * once to float.  Mode defaults to LBM_MODE_STREAM.  LBM_D3Q343 is not
+ * supported by this version (LBM_EINVAL). */
+int lbm_create(int D, int lattice, int n, double tau, lbm_handle *out);
+
+/* Select the transport mode (lbm_mode) and, for LBM_MODE_FD, the number m
+ * >= 1 of forward-Euler sub-steps per lattice time dx/r (Eq. DisEvolSpaTiI).
+ * Must be called before lbm_set_grid. */
+int lbm_set_mode(lbm_handle h, int mode, int m_fd);
+
+/* Set the grid: shape[0..D-1] = X (fastest), Y, Z, each >= 1 (Y, Z <= 65535);
+ * bc[0..D-1] per-axis boundary (periodic wrap, or copy = zero-gradient
+ * clamp to the edge node, the paper's "open" boundary of Sec. VI).  Returns
+ * the bytes needed for each of the two state buffers and for the work
+ * buffer. */
+int lbm_set_grid(lbm_handle h, const int64_t *shape, const int *bc,
+                 size_t *state_bytes, size_t *work_bytes);
+
+/* Bind caller-owned device memory: two state buffers (ping-pong) of
+ * state_bytes each, a work buffer of work_bytes, and the CUDA stream
+ * (cudaStream_t, NULL = legacy default) all later work is enqueued on.
+ * Clears the sticky status flag (asynchronously, on that stream). */
+int lbm_bind(lbm_handle h, void *buf_a, void *buf_b, size_t state_bytes, void *work,
+             size_t work_bytes, void *stream);
+
+/* Equilibrium initial state from the macroscopic fields (device pointers,
+ * layout above): h_j = h_j^eq(T); in STREAM mode the stored ft is the pull
+ * pre-image ft_i(x) = g_i^eq(m0(bc(x + e_i))), in FD mode ft_i = g_i^eq(m0(x)).
+ * Asynchronous.  Resets the step counter. */
+int lbm_set_macro(lbm_handle h, const float *rho, const float *u, const float *T);
+
+/* Advance k >= 0 steps (Sec. V steps 1-5): one fused kernel launch per step.
+ * Asynchronous. */
+int lbm_step(lbm_handle h, int64_t k);
+
+/* rho, u, T of the current state (Sec. V steps 3-4, Eq. T) into device
+ * arrays (layout above).  Asynchronous. */
+int lbm_get_moments(lbm_handle h, float *rho, float *u, float *T);
+
+/* Global diagnostics of the current state, accumulated in double precision
+ * with a fixed reduction order: out[0] = sum rho, out[1..D] = sum rho u_a,
+ * out[D+1] = sum rho (E + u^2/2) (the total energy of Eq. Total),
+ * out[D+2] = max over nodes of |sum_j h_j - 1| (Eq. FFeqRhoEta).  out is a
+ * HOST pointer to D+3 doubles.  Synchronizing.  Returns LBM_ENONFINITE if the
+ * sticky flag is set (out is still written). */
+int lbm_conservation(lbm_handle h, double *out);
+
+/* Copy the stored populations to / from device arrays in canonical order:
+ * ft[i*N + node] for i < Q_t, fr[j*N + node] for j < Q_r (fr ignored when
+ * n = 0).  In STREAM mode ft holds post-collision values (the pull source).
+ * Asynchronous.  Used for checkpoint/resume and per-population checks. */
+int lbm_get_state(lbm_handle h, float *ft, float *fr);
+int lbm_set_state(lbm_handle h, const float *ft, const float *fr);
+
+/* Sticky device status: LBM_OK or LBM_ENONFINITE.  Synchronizing. */
+int lbm_status(lbm_handle h);
+
+/* Steps taken since the last lbm_set_macro / lbm_set_state. */
+int64_t lbm_steps(lbm_handle h);
+
+/* Human-readable message for the last error on this handle ("" if none). */
+const char *lbm_last_error(lbm_handle h);
+
+/* The library's own lattice constants (Tables I, II as re-solved here, in
+ * double precision before rounding): r, e[Q*3] (ints), w[Q].  Returns Q, or
+ * a negative lbm_status.  Host only; needs no GPU. */
+int lbm_lattice_info(int lattice, double *r, int *e, double *w);
+
+/* Number of kernel launches this handle has enqueued since creation. */
+int64_t lbm_launch_count(lbm_handle h);
+
+void lbm_destroy(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */
