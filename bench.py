@@ -1,0 +1,320 @@
+"""Throughput of the fused collide-and-stream step (Mnode-updates/s, ft+fr).
+
+Workload: the four-quadrant 2-D Riemann problem on 2048 x 2048 nodes, D2Q49
+translational + D1Q7 rotational populations (gamma = 1.4, n = 3), tau = 2/3,
+periodic, float32, STREAM transport -- the stable-envelope variant of the
+seeded quadrant draws (see workloads.riemann_2d).  A step is one fused kernel
+launch over all nodes.  The state (2 x 940 MB) is larger than L2, so no flush
+is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU runs (torchrun) are independent replicas, one per GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mnode-updates/s (f+g)"
+X = Y = 2048
+LATTICE, NROT, TAU = "D2Q49", 3, 2.0 / 3.0
+QT, QR = 49, 7
+BYTES_PER_NODE = (QT + QR) * 4 * 2          # every population read once, written once
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_step launch of this
+# workload (profiles/k_step_d2q49_stream_2048x2048.md); None until captured
+# for the current kernel.
+NCU_TRAFFIC_BYTES = None
+REF_SAMPLE = 512                             # oracle sample grid for the CPU arms
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[2:]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(seconds: float = 12.0, size: int = REF_SAMPLE, max_steps: int = 10**9):
+    """Oracle Mnode-updates/s on a size x size sample of the same workload."""
+    from oracle import oracle
+    from paper_1606_06107_gb300 import workloads
+
+    wl = workloads.riemann_2d(size, size, seed=0, mild=True)
+    sim = oracle.Sim(oracle.D2Q49, wl.n, wl.tau, wl.shape, (oracle.PERIODIC,) * 2)
+    sim.set_macro(wl.rho, wl.u, wl.T)
+    sim.step(1)  # warm-up (page-in, thread pool)
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        sim.step(1)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return size * size * steps / dt / 1e6, steps, dt, threads
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_1606_06107_gb300 import workloads
+
+    # size the per-step sample so the whole run stays near 90 s of CPU time
+    rate, _, _, _ = cpu_oracle_rate(seconds=2.0, size=128)
+    side = int(np.sqrt(rate * 1e6 * 90.0 / (args.steps + args.warmup)))
+    side = max(32, min(REF_SAMPLE, side // 2 * 2))
+    wl = workloads.riemann_2d(side, side, seed=0, mild=True)
+    sim = oracle.Sim(oracle.D2Q49, wl.n, wl.tau, wl.shape, (oracle.PERIODIC,) * 2)
+    sim.set_macro(wl.rho, wl.u, wl.T)
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = side * side * args.steps / dt / 1e6
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mnode-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"riemann_2d_mild {side}x{side} sample of the "
+                   f"{X}x{Y} D2Q49+D1Q7 n=3 periodic STREAM problem (FP64 CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": "Mnode-updates/s", "cores": threads,
+                         "kind": "oracle",
+                         "sample": f"{side}x{side} grid, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "Mnode-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_1606_06107_gb300 import Lbm, workloads
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    X = Y = args.size
+    wl = workloads.riemann_2d(X, Y, seed=rank, mild=not args.stated)
+    stream = torch.cuda.current_stream()
+    sim = Lbm(LATTICE, NROT, TAU, (X, Y), ("periodic", "periodic"), device=dev, stream=stream)
+    rho = torch.tensor(wl.rho, dtype=torch.float32).pin_memory()
+    u = torch.tensor(wl.u, dtype=torch.float32).pin_memory()
+    T = torch.tensor(wl.T, dtype=torch.float32).pin_memory()
+    sim.set_macro(rho.to(dev), u.to(dev), T.to(dev))
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region: K fused steps -------------------------
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    l0 = sim.launches
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_begin = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_begin.record(stream)
+        for k in range(args.steps):
+            starts[k].record(stream)
+            sim.step(1)
+            ends[k].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = sim.launches - l0
+    elapsed = t_begin.elapsed_time(t_end) / 1e3
+    per_launch = [s.elapsed_time(e) / 1e3 for s, e in zip(starts, ends)]
+    status = sim.status()
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+
+    nodes = X * Y
+    value = nodes * args.steps * world / elapsed / 1e6
+    hbm, peak_kind = peaks()
+    avg_launch = float(np.mean(per_launch))
+    achieved = BYTES_PER_NODE * nodes / avg_launch / 1e9
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    # pinned host fields -> device -> set_macro; every step: one fused step and
+    # a 4-byte read of the device status word; at the end the moments go back
+    # to pinned host memory.
+    e2e_steps = args.steps
+    rho_o = torch.empty(nodes, dtype=torch.float32).pin_memory()
+    u_o = torch.empty(2, nodes, dtype=torch.float32).pin_memory()
+    T_o = torch.empty(nodes, dtype=torch.float32).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_macro(rho.to(dev, non_blocking=True), u.to(dev, non_blocking=True),
+                  T.to(dev, non_blocking=True))
+    for _ in range(e2e_steps):
+        sim.step(1)
+        sim.status()
+    r_d, u_d, T_d = sim.moments()
+    rho_o.copy_(r_d, non_blocking=True)
+    u_o.copy_(u_d, non_blocking=True)
+    T_o.copy_(T_d, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+    field_bytes = 4 * nodes * 4  # rho, u_x, u_y, T
+    e2e = {"value": nodes * e2e_steps * world / e2e_dt / 1e6, "unit": "Mnode-updates/s",
+           "h2d_bytes_per_step": field_bytes / e2e_steps,
+           "d2h_bytes_per_step": 4 + field_bytes / e2e_steps}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        rate, steps, dt, threads = cpu_oracle_rate()
+        cpu = {"value": rate, "unit": "Mnode-updates/s", "cores": threads, "kind": "oracle",
+               "sample": f"{REF_SAMPLE}x{REF_SAMPLE} grid of the same problem, {steps} "
+                         f"steps in {dt:.1f} s (FP64)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mnode-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{wl.name} {X}x{Y} {LATTICE}+D1Q7 n={NROT} tau=2/3 periodic "
+                               f"STREAM, seed=rank", "nodes_per_gpu": nodes,
+                   "bytes_per_node_step": BYTES_PER_NODE,
+                   "l2": "inputs larger than L2 (2 x 940 MB state), no flush",
+                   "parallelism": f"replicas x{world}", "status": status},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind,
+                     "traffic": NCU_TRAFFIC_BYTES, "kernel": "k_step<D2Q49,rot,STREAM>",
+                     "avg_launch_ms": avg_launch * 1e3},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--stated", action="store_true",
+                    help="use the stated quadrant draws (goes non-finite) instead of the "
+                         "stable-envelope variant")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--size", type=int, default=X, help="grid edge (profiling of smaller cases)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -75,27 +75,37 @@ def paper_tube_2d(X: int = 1000, Y: int = 16, kind: str = "D2Q37",
 
 
 def riemann_2d(X: int = 2048, Y: int = 2048, seed: int = 0, kind: str = "D2Q49",
-               steps: int = 5000, t_range=None) -> Workload:
-    """Four-quadrant 2-D Riemann problem: per quadrant rho ~ U[0.1, 1.5],
-    p ~ U[0.03, 1.5], |u| <= 0.5 (uniform angle, radius ~ U[0, 0.5]); gamma=1.4
-    (D=2, n=3); tau=2/3; periodic.  With ``t_range=(lo, hi)`` the pressure is
-    redrawn as p = rho * U[lo, hi] (the stable-envelope variant)."""
+               steps: int = 5000, mild: bool = False) -> Workload:
+    """Four-quadrant 2-D Riemann problem, gamma=1.4 (D=2, n=3), tau=2/3,
+    periodic.  Per quadrant, drawn from the seed: rho ~ U[0.1, 1.5],
+    p ~ U[0.03, 1.5] and a velocity of uniform direction with |u| ~ U[0, 0.5].
+
+    ``mild=True`` is the stable-envelope variant (the 4th-order lattices are
+    reliable near T = 1; the stated draws reach T = p/rho of 0.02..15 and
+    density ratios near 10, where the scheme goes non-finite within a few
+    steps): rho ~ U[0.7, 1.3], T ~ U[0.7, 1.3], |u| ~ U[0, 0.2].
+    """
     rng = np.random.Generator(np.random.PCG64(seed))
-    rho_q = rng.uniform(0.1, 1.5, 4)
-    p_q = rng.uniform(0.03, 1.5, 4)
+    if mild:
+        rho_q = rng.uniform(0.7, 1.3, 4)
+        T_q = rng.uniform(0.7, 1.3, 4)
+        umax = 0.2
+    else:
+        rho_q = rng.uniform(0.1, 1.5, 4)
+        T_q = rng.uniform(0.03, 1.5, 4) / rho_q
+        umax = 0.5
     ang = rng.uniform(0.0, 2.0 * np.pi, 4)
-    rad = rng.uniform(0.0, 0.5, 4)
-    if t_range is not None:
-        p_q = rho_q * rng.uniform(t_range[0], t_range[1], 4)
+    rad = rng.uniform(0.0, umax, 4)
     ux_q = rad * np.cos(ang)
     uy_q = rad * np.sin(ang)
     xs = np.arange(X) >= X // 2
     ys = np.arange(Y) >= Y // 2
     quad = (ys[:, None].astype(int) * 2 + xs[None, :].astype(int))  # [Y, X] in 0..3
     rho = rho_q[quad]
-    T = p_q[quad] / rho
+    T = T_q[quad]
     u = np.stack([ux_q[quad], uy_q[quad]])
-    return Workload("riemann_2d", kind, 3, 2.0 / 3.0, (X, Y), ("periodic", "periodic"),
+    name = "riemann_2d_mild" if mild else "riemann_2d"
+    return Workload(name, kind, 3, 2.0 / 3.0, (X, Y), ("periodic", "periodic"),
                     rho, u, T, steps)
 
 

@@ -1,0 +1,94 @@
+"""The C-ABI library loads, exports every symbol include/lbm.h declares, and
+validates its arguments -- all without a GPU (no compute calls here).  Its
+lattice constants, solved by its own method, agree with the oracle's."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "lbm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lbmlib):
+    from paper_1606_06107_gb300 import lbm
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lbmlib, name), name
+        assert name in lbm.SIGNATURES, name
+
+
+@pytest.mark.parametrize("name,kind", [("D1Q7", 1), ("D2Q37", 2), ("D2Q49", 3)])
+def test_library_lattice_matches_oracle(lbmlib, orc, name, kind):
+    from paper_1606_06107_gb300 import lbm
+    r, e, w = lbm.lattice_info(name)
+    ro, eo, wo, _ = orc.lattice(kind)
+    assert abs(r - ro) < 1e-13
+    assert np.array_equal(e, eo)
+    assert np.allclose(w, wo, rtol=1e-12, atol=1e-16)
+
+
+def _create(lib, D, lattice, n, tau):
+    h = ctypes.c_void_p()
+    rc = lib.lbm_create(D, lattice, n, tau, ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("args", [(0, 1, 4, 0.7), (2, 1, 4, 0.7), (1, 1, -1, 0.7), (1, 1, 4, 0.0),
+                                  (1, 1, 4, -1.0), (2, 9, 3, 0.7), (3, 4, 0, 0.7),
+                                  (1, 1, 4, float("nan"))])
+def test_create_rejects_bad_arguments(lbmlib, args):
+    rc, h = _create(lbmlib, *args)
+    assert rc == -1 and not h.value
+
+
+def test_grid_validation_and_sizes(lbmlib):
+    rc, h = _create(lbmlib, 2, 3, 3, 2 / 3)
+    assert rc == 0
+    try:
+        sb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+        shape = (ctypes.c_int64 * 3)(1000, 70000, 1)
+        bc = (ctypes.c_int * 3)(0, 1, 0)
+        assert lbmlib.lbm_set_grid(h, shape, bc, ctypes.byref(sb), ctypes.byref(wb)) == -2
+        shape = (ctypes.c_int64 * 3)(1000, 16, 1)
+        bad_bc = (ctypes.c_int * 3)(0, 7, 0)
+        assert lbmlib.lbm_set_grid(h, shape, bad_bc, ctypes.byref(sb), ctypes.byref(wb)) == -1
+        assert lbmlib.lbm_set_grid(h, shape, bc, ctypes.byref(sb), ctypes.byref(wb)) == 0
+        assert sb.value == 4 * (49 + 7) * 1024 * 16      # rows padded to 32 floats
+        assert wb.value > 0
+        assert lbmlib.lbm_set_mode(h, 1, 10) == -6       # mode after grid: out of order
+        assert lbmlib.lbm_step(h, 1) == -6               # no state yet
+        assert lbmlib.lbm_step(h, -1) == -1
+        assert b"lbm_set_macro" in lbmlib.lbm_last_error(h) or lbmlib.lbm_last_error(h)
+    finally:
+        lbmlib.lbm_destroy(h)
+
+
+def test_mode_validation(lbmlib):
+    rc, h = _create(lbmlib, 1, 1, 4, 2 / 3)
+    assert rc == 0
+    try:
+        assert lbmlib.lbm_set_mode(h, 1, 0) == -1
+        assert lbmlib.lbm_set_mode(h, 5, 1) == -1
+        assert lbmlib.lbm_set_mode(h, 1, 10) == 0
+    finally:
+        lbmlib.lbm_destroy(h)
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The package never imports or links the oracle (test infrastructure)."""
+    pkg = os.path.join(os.path.dirname(HEADER), "..", "paper_1606_06107_gb300")
+    pat = re.compile(r"^\s*(import|from)\s+oracle\b|liborc|lbm_oracle", re.M)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                assert not pat.search(open(os.path.join(root, f)).read()), f

@@ -1,0 +1,252 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances.  The GPU computes in float32; one step rounds each population a
+few tens of times (unit roundoff 6e-8), so a single step is compared
+population by population within 1e-5 of each population array's magnitude.
+After many steps the bar is the one stated for the method: relative L1 error
+<= 1e-5 in rho, u and T, and L-infinity <= 1e-3 at a shock.
+"""
+import numpy as np
+import pytest
+
+from paper_1606_06107_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+KIND = {"D1Q7": 1, "D2Q37": 2, "D2Q49": 3}
+BC = {"periodic": 0, "copy": 1}
+
+
+def make_pair(orc, wl, mode="stream", m_fd=10):
+    from paper_1606_06107_gb300 import Lbm
+    gpu = Lbm(wl.kind, wl.n, wl.tau, wl.shape, wl.bc, mode=mode, m_fd=m_fd)
+    ref = orc.Sim(KIND[wl.kind], wl.n, wl.tau, wl.shape, tuple(BC[b] for b in wl.bc),
+                  mode=0 if mode == "stream" else 1, m_fd=m_fd)
+    return gpu, ref
+
+
+def start_equal(gpu, ref, wl):
+    """Oracle initial state, rounded to float32 on both sides."""
+    ref.set_macro(wl.rho, wl.u, wl.T)
+    ft, fr = ref.state()
+    ft32 = ft.astype(np.float32)
+    fr32 = fr.astype(np.float32)
+    ref.set_state(ft32.astype(np.float64), fr32.astype(np.float64) if ref.Qr else None)
+    gpu.set_state(ft32, fr32 if ref.Qr else None)
+
+
+def fields(gpu):
+    return [x.cpu().numpy().astype(np.float64) for x in gpu.moments()]
+
+
+def rel_l1(a, b):
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def assert_state_close(gpu, ref, tol=1e-5):
+    ft, fr = (x.cpu().numpy().astype(np.float64) for x in gpu.state())
+    ft_r, fr_r = ref.state()
+    for i in range(ft.shape[0]):
+        scale = np.abs(ft_r[i]).max()
+        err = np.abs(ft[i] - ft_r[i]).max()
+        assert err <= tol * scale + 1e-30, (i, err, scale)
+    for j in range(fr.shape[0]):
+        scale = np.abs(fr_r[j]).max()
+        assert np.abs(fr[j] - fr_r[j]).max() <= tol * scale + 1e-30, j
+
+
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,shape,mode", [("D1Q7", (1000,), "stream"), ("D1Q7", (37,), "fd"),
+                                             ("D2Q37", (61, 9), "stream"),
+                                             ("D2Q49", (130, 7), "stream"),
+                                             ("D2Q49", (33, 5), "fd")])
+def test_set_macro_round_trip(orc, kind, shape, mode):
+    from paper_1606_06107_gb300 import Lbm
+    wl = workloads.smooth_random(shape, seed=1, kind=kind, n=3)
+    gpu = Lbm(kind, wl.n, wl.tau, shape, wl.bc, mode=mode)
+    gpu.set_macro(wl.rho, wl.u, wl.T)
+    rho, u, T = fields(gpu)
+    assert np.abs(rho - wl.rho.ravel()).max() < 2e-6
+    assert np.abs(u - wl.u.reshape(len(shape), -1)).max() < 2e-6
+    assert np.abs(T - wl.T.ravel()).max() < 2e-6
+
+
+ONE_STEP = [
+    ("D1Q7", (1,), ("periodic",), "stream", 4), ("D1Q7", (2,), ("copy",), "stream", 4),
+    ("D1Q7", (3,), ("periodic",), "fd", 2), ("D1Q7", (37,), ("copy",), "stream", 0),
+    ("D1Q7", (129,), ("periodic",), "stream", 7), ("D1Q7", (200,), ("copy",), "fd", 4),
+    ("D2Q37", (13, 5), ("copy", "periodic"), "stream", 3),
+    ("D2Q37", (40, 3), ("periodic", "copy"), "fd", 3),
+    ("D2Q49", (33, 7), ("periodic", "periodic"), "stream", 3),
+    ("D2Q49", (129, 2), ("copy", "copy"), "stream", 0),
+    ("D2Q49", (17, 11), ("periodic", "copy"), "fd", 5),
+    ("D2Q49", (7, 1), ("periodic", "periodic"), "stream", 3),
+]
+
+
+@pytest.mark.parametrize("kind,shape,bc,mode,n", ONE_STEP)
+def test_one_step_per_population(orc, kind, shape, bc, mode, n):
+    """Every stored population after one step, on ragged and degenerate
+    grids (1, 2, 3 nodes along an axis; partial 128-wide tiles)."""
+    wl = workloads.smooth_random(shape, seed=3, kind=kind, n=n, bc=bc)
+    gpu, ref = make_pair(orc, wl, mode, m_fd=4)
+    start_equal(gpu, ref, wl)
+    gpu.step(1)
+    ref.step(1)
+    assert_state_close(gpu, ref)
+    gpu.step(2)
+    ref.step(2)
+    assert_state_close(gpu, ref, tol=3e-5)
+
+
+def test_1000_steps_2d_stream(orc):
+    """D2Q49 + D1Q7, 64 x 48 periodic, 1000 steps (several 128-wide tiles
+    are not needed here; the ragged-tile cases are covered above)."""
+    wl = workloads.smooth_random((64, 48), seed=5, kind="D2Q49", n=3)
+    gpu, ref = make_pair(orc, wl)
+    start_equal(gpu, ref, wl)
+    gpu.step(1000)
+    ref.step(1000)
+    assert gpu.status() == 0
+    for a, b in zip(fields(gpu), ref.moments()):
+        assert rel_l1(a, b) <= 1e-5
+
+
+def test_1000_steps_sod_fd(orc):
+    """Sod's tube (1000 nodes, D1Q7 + D1Q7, n = 4, copy ends), the paper's
+    forward-Euler upwind transport with m = 10: rel-L1 <= 1e-5 and
+    L-infinity <= 1e-3 through the shock after 1000 steps."""
+    wl = workloads.sod_1d()
+    gpu, ref = make_pair(orc, wl, mode="fd", m_fd=10)
+    start_equal(gpu, ref, wl)
+    gpu.step(1000)
+    ref.step(1000)
+    assert gpu.status() == 0
+    for a, b in zip(fields(gpu), ref.moments()):
+        assert rel_l1(a, b) <= 1e-5
+        assert rel_linf(a, b) <= 1e-3
+
+
+def test_1000_steps_weak_tube_stream_1d(orc):
+    """A 1-D shock tube within the STREAM scheme's stable range (pressure
+    ratio 2.5), 1000 nodes, copy ends, 1000 steps."""
+    from paper_1606_06107_gb300.workloads import Workload, _two_state_1d
+    rho, u, T = _two_state_1d(1000, (1.0, 0.0, 1.0), (0.5, 0.0, 0.4))
+    wl = Workload("weak_tube", "D1Q7", 4, 2 / 3, (1000,), ("copy",), rho, u[None], T, 1000)
+    gpu, ref = make_pair(orc, wl)
+    start_equal(gpu, ref, wl)
+    gpu.step(1000)
+    ref.step(1000)
+    for a, b in zip(fields(gpu), ref.moments()):
+        assert rel_l1(a, b) <= 1e-5
+        assert rel_linf(a, b) <= 1e-3
+
+
+def test_paper_tube_d2q37_stream(orc):
+    """The paper's own run (Sec. VI): 1000 x 16, D2Q37 + D1Q7, 180 steps."""
+    wl = workloads.paper_tube_2d(kind="D2Q37")
+    gpu, ref = make_pair(orc, wl)
+    start_equal(gpu, ref, wl)
+    gpu.step(180)
+    ref.step(180)
+    for a, b in zip(fields(gpu), ref.moments()):
+        assert rel_l1(a, b) <= 1e-5
+        assert rel_linf(a, b) <= 1e-3
+
+
+def test_conservation_matches_oracle(orc):
+    wl = workloads.smooth_random((96, 40), seed=9, kind="D2Q49", n=3)
+    gpu, ref = make_pair(orc, wl)
+    start_equal(gpu, ref, wl)
+    gpu.step(10)
+    ref.step(10)
+    cg = gpu.conservation()
+    cr = ref.conservation()
+    assert abs(cg[0] - cr[0]) < 1e-6 * cr[0]
+    assert np.all(np.abs(cg[1:3] - cr[1:3]) < 1e-6 * cr[0])
+    assert abs(cg[3] - cr[3]) < 1e-6 * cr[3]
+    assert cg[4] < 1e-5
+
+
+def test_determinism_and_resume(orc):
+    """Two runs are bitwise identical, and a checkpoint taken after 7 steps
+    and resumed in a new instance reaches the same state after 13."""
+    from paper_1606_06107_gb300 import Lbm
+    wl = workloads.smooth_random((150, 20), seed=2, kind="D2Q37", n=3)
+    a = Lbm(wl.kind, wl.n, wl.tau, wl.shape, wl.bc)
+    b = Lbm(wl.kind, wl.n, wl.tau, wl.shape, wl.bc)
+    a.set_macro(wl.rho, wl.u, wl.T)
+    b.set_macro(wl.rho, wl.u, wl.T)
+    a.step(20)
+    b.step(7)
+    ft, fr = b.state()
+    c = Lbm(wl.kind, wl.n, wl.tau, wl.shape, wl.bc)
+    c.set_state(ft, fr)
+    c.step(13)
+    sa = [x.cpu().numpy() for x in a.state()]
+    sc = [x.cpu().numpy() for x in c.state()]
+    assert all(np.array_equal(x, y) for x, y in zip(sa, sc))
+    assert np.array_equal(a.conservation(), c.conservation())
+
+
+def test_step_zero_and_split_steps():
+    from paper_1606_06107_gb300 import Lbm
+    wl = workloads.smooth_random((70,), seed=4, kind="D1Q7", n=2)
+    a = Lbm(wl.kind, wl.n, wl.tau, wl.shape, wl.bc)
+    b = Lbm(wl.kind, wl.n, wl.tau, wl.shape, wl.bc)
+    for s in (a, b):
+        s.set_macro(wl.rho, wl.u, wl.T)
+    a.step(0)
+    a.step(5)
+    for _ in range(5):
+        b.step(1)
+    assert a.steps == b.steps == 5
+    assert all(np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+               for x, y in zip(a.state(), b.state()))
+
+
+def test_nonfinite_flag_is_reported_not_trapped():
+    """A non-positive temperature sets the sticky status flag; the kernels
+    keep running and the context stays usable."""
+    from paper_1606_06107_gb300 import Lbm, LbmError
+    wl = workloads.smooth_random((64,), seed=4, kind="D1Q7", n=4)
+    T = wl.T.copy()
+    T[10] = -1.0
+    s = Lbm(wl.kind, wl.n, wl.tau, wl.shape, wl.bc)
+    s.set_macro(wl.rho, wl.u, T)
+    s.step(2)
+    assert s.status() == -4
+    with pytest.raises(LbmError):
+        s.conservation()
+    ok = Lbm(wl.kind, wl.n, wl.tau, wl.shape, wl.bc)
+    ok.set_macro(wl.rho, wl.u, wl.T)
+    ok.step(2)
+    assert ok.status() == 0
+
+
+def test_full_size_bench_config_sampled(orc):
+    """At the benchmark's full size (2048 x 2048, D2Q49 + D1Q7, periodic,
+    the launch configuration bench.py times): after 20 GPU steps one more
+    GPU step is compared with one oracle step from the same float32 state,
+    population by population; mass and momentum stay conserved."""
+    import torch
+    wl = workloads.riemann_2d(2048, 2048, seed=0, mild=True)
+    gpu, ref = make_pair(orc, wl)
+    gpu.set_macro(wl.rho, wl.u, wl.T)
+    c0 = gpu.conservation()
+    gpu.step(20)
+    ft, fr = (x.cpu().numpy().astype(np.float64) for x in gpu.state())
+    ref.set_state(ft, fr)
+    del ft, fr
+    gpu.step(1)
+    ref.step(1)
+    torch.cuda.synchronize()
+    assert_state_close(gpu, ref)
+    c1 = gpu.conservation()
+    assert abs(c1[0] - c0[0]) < 1e-6 * c0[0]
+    assert np.all(np.abs(c1[1:3] - c0[1:3]) < 1e-6 * c0[0])
