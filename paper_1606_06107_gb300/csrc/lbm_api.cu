@@ -248,10 +248,16 @@ Args make_args(const lbm_ctx *h)
     for (int k = 0; k < 3; ++k) a.bc[k] = h->bc[k];
     const double m = (h->mode == LBM_MODE_FD) ? h->m_fd : 1.0;
     a.r = (float)h->r;
-    a.omega = (float)(1.0 / (m * h->tau));
+    // omega and 1 - omega must both be exact floats: the kernels keep
+    // (1 - omega) g and add omega g^eq, and a rounded 1 - omega would create
+    // or destroy mass at ~1e-8 per step.  Nudge omega by at most half an ulp.
+    const float om = (float)(1.0 / (m * h->tau));
+    const float keep = (float)(1.0 - (double)om);
+    a.omega = (float)(1.0 - (double)keep);
     a.nu_scale = (float)(1.0 / (m * h->r));
-    a.cT = (float)(2.0 / (h->D + h->n));
+    a.cT = (float)(0.5 * (h->D + h->n));  // T = (energy per mass) / ((D+n)/2), Eq. T
     a.half_n_r2 = (float)(0.5 * h->n * h->r * h->r);
+    a.half_n = (float)(0.5 * h->n);
     a.inv_m = (float)(1.0 / m);
     for (int i = 0; i < h->Q; ++i) a.w[i] = (float)h->w[i];
     for (int j = 0; j < 7; ++j) a.wr[j] = (float)h->wr[j];
@@ -382,7 +388,9 @@ int lbm_set_grid(lbm_handle h, const int64_t *shape, const int *bc, size_t *stat
         return fail(h, LBM_ESIZE, "X <= 2^30 and Y, Z <= 65535 are required");
     const int64_t pitch = (s[0] + 31) / 32 * 32;
     const int64_t S = pitch * s[1] * s[2];
-    if (S > 0x7fffffffLL) return fail(h, LBM_ESIZE, "padded grid exceeds 2^31 nodes");
+    // the kernels index the whole state buffer with 32-bit element offsets
+    if (S * (h->Q + h->Qr) > 0x7fffffffLL)
+        return fail(h, LBM_ESIZE, "state buffer would exceed 2^31 floats");
     for (int a = 0; a < 3; ++a) {
         h->shape[a] = s[a];
         h->bc[a] = b[a];

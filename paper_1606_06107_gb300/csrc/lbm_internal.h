@@ -26,7 +26,7 @@ struct Args {
     int64_t S;  // population stride in floats (pitch * Y * Z)
     int64_t N;  // nodes (X * Y * Z)
     int bc[3];
-    float r, omega, nu_scale, cT, half_n_r2, inv_m;
+    float r, omega, nu_scale, cT, half_n, half_n_r2, inv_m;
     float w[kMaxQ];
     float wr[7];
     const float *src;  // current state (Step reads, Moments/Conserve/GetState read)

