@@ -128,6 +128,30 @@ int lbm_get_moments(lbm_handle h, float *rho, float *u, float *T);
  * sticky flag is set (out is still written). */
 int lbm_conservation(lbm_handle h, double *out);
 
+/* The sums of lbm_conservation for callers that cannot provide device
+ * scratch memory (the paper has no counterpart; this is a library service).
+ * A host application that owns all device memory itself -- its allocator has
+ * reserved the GPU, or its memory budget is fixed before the run -- can pass
+ * a state buffer here without binding a work buffer.  The per-block partial
+ * sums live in a static device array inside the library (65,600 bytes, held
+ * on every GPU that loads the library until the process exits); nothing is
+ * allocated.
+ *   state  device pointer to one state buffer in the layout lbm_set_grid
+ *          describes (256-byte aligned), on the current device.  For a bound
+ *          handle, the current state is buf_a after an even number of steps
+ *          since lbm_set_macro / lbm_set_state and buf_b after an odd number.
+ *   stream cudaStream_t the work is enqueued on (NULL = legacy default).
+ *   out    HOST pointer to D+3 doubles, filled as by lbm_conservation.
+ * Needs lbm_set_grid, not lbm_bind; does not read the sticky status flag.
+ * Synchronizing (waits for `stream`).  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array: calls that overlap on the GPU (different streams or host
+ * threads, same device) race and may return wrong sums.  Returns LBM_ESIZE if
+ * the reduction would need more than the array's 1024 block records (more
+ * than 256 SMs), LBM_EINVAL for null or misaligned pointers. */
+int lbm_conservation_noalloc(lbm_handle h, const void *state, void *stream, double *out);
+
 /* Copy the stored populations to / from device arrays in canonical order:
  * ft[i*N + node] for i < Q_t, fr[j*N + node] for j < Q_r (fr ignored when
  * n = 0).  In STREAM mode ft holds post-collision values (the pull source).

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include <cuda_runtime.h>
@@ -575,3 +576,102 @@ const char *lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : "null han
 void lbm_destroy(lbm_handle h) { delete h; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Conservation sums without any caller-provided scratch.
+//
+// lbm_conservation needs the work buffer bound with lbm_bind for its
+// per-block partial sums.  Some callers cannot provide one: a host
+// application that hands this library a state buffer but owns all device
+// memory itself (its allocator has reserved the GPU, or its memory budget is
+// fixed before the run), or a checker that inspects a saved state outside
+// any bound solver.  lbm_conservation_noalloc serves them: its scratch is the
+// file-scope array below, which every GPU that loads this library holds until
+// the process exits, and it never calls cudaMalloc, cudaFree or any other
+// allocating routine.
+
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 1024;  // reduction blocks the array can hold
+constexpr int kNoAllocMaxDevices = 64;
+
+// kNoAllocMaxBlocks partial records, then one record for the final sums
+// (kRedSlots doubles each): 65,600 bytes.  In host code this name is only a
+// stand-in for the device array; its device address comes from
+// cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_scratch[(kNoAllocMaxBlocks + 1) * lbm::kRedSlots];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (with that device current) and cached.
+cudaError_t noalloc_scratch(int dev, double **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int lbm_conservation_noalloc(lbm_handle h, const void *state, void *stream, double *out)
+{
+    if (!h) return LBM_EINVAL;
+    if (!h->grid_set) return fail(h, LBM_ESTATE, "lbm_set_grid must precede lbm_conservation_noalloc");
+    if (!state || !out) return fail(h, LBM_EINVAL, "null state or output");
+    if (!aligned256(state)) return fail(h, LBM_EINVAL, "state must be 256-byte aligned");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(h, LBM_EINVAL, "device ordinal too large");
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceGetAttribute");
+    const int64_t want = std::min<int64_t>((h->N + lbm::kRedThreads - 1) / lbm::kRedThreads, 4LL * sms);
+    const int blocks = (int)std::max<int64_t>(1, want);
+    if (blocks > kNoAllocMaxBlocks)
+        return fail(h, LBM_ESIZE, "the reduction needs " + std::to_string(blocks) +
+                                      " blocks of scratch; the static array holds " +
+                                      std::to_string(kNoAllocMaxBlocks));
+    double *scratch = nullptr;
+    e = noalloc_scratch(dev, &scratch);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+
+    // Each block overwrites all of its partial record and the final kernel
+    // overwrites the result record, so nothing left by an earlier call is
+    // read and nothing needs clearing first.
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Args a = make_args(h);
+    a.src = static_cast<const float *>(state);
+    a.partials = scratch;
+    a.red_blocks = blocks;
+    a.status = nullptr;
+    switch (h->lattice) {
+    case LBM_D1Q7: e = lbm::launch_d1q7(Op::Conserve, a, s); break;
+    case LBM_D2Q37: e = lbm::launch_d2q37(Op::Conserve, a, s); break;
+    case LBM_D2Q49: e = lbm::launch_d2q49(Op::Conserve, a, s); break;
+    default: e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "conservation kernel");
+    double *result = scratch + (size_t)kNoAllocMaxBlocks * lbm::kRedSlots;
+    k_finalize<<<1, lbm::kRedThreads, 0, s>>>(scratch, blocks, result);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "finalize kernel");
+    h->launches += 2;
+    double res[lbm::kRedSlots];
+    e = cudaMemcpyAsync(res, result, sizeof(res), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "conservation readback");
+    out[0] = res[0];
+    for (int d = 0; d < h->D; ++d) out[1 + d] = res[1 + d];
+    out[1 + h->D] = res[4];
+    out[2 + h->D] = res[5];
+    return LBM_OK;
+}

@@ -39,6 +39,7 @@ SIGNATURES = {
     "lbm_step": (ctypes.c_int, [_vp, _i64]),
     "lbm_get_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lbm_conservation": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "lbm_conservation_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "lbm_get_state": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbm_set_state": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbm_status": (ctypes.c_int, [_vp]),
