@@ -32,9 +32,10 @@ LATTICE, NROT, TAU = "D2Q49", 3, 2.0 / 3.0
 QT, QR = 49, 7
 BYTES_PER_NODE = (QT + QR) * 4 * 2          # every population read once, written once
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_step launch of this
-# workload (profiles/k_step_d2q49_stream_2048x2048.md); None until captured
-# for the current kernel.
-NCU_TRAFFIC_BYTES = None
+# workload, scaled by node count from a 1024^2 capture of the same kernel
+# (profiles/k_step_d2q49_stream_2048x2048.md); None whenever the kernel has
+# changed since that capture.
+NCU_TRAFFIC_BYTES = 1.693e9
 REF_SAMPLE = 512                             # oracle sample grid for the CPU arms
 
 
