@@ -36,8 +36,7 @@ struct lbm_ctx {
     char *work = nullptr;
     cudaStream_t stream = nullptr;
     int device = 0;
-    int red_blocks = 1;
-    int64_t steps = 0;
+    int red_blocks = 1;    int64_t steps = 0;
     int64_t launches = 0;
     std::string err;
 };
@@ -517,6 +516,7 @@ int lbm_conservation(lbm_handle h, double *out)
     for (int d = 0; d < h->D; ++d) out[1 + d] = res[1 + d];
     out[1 + h->D] = res[4];
     out[2 + h->D] = res[5];
+    if (status & 2) return fail(h, LBM_ETIMEOUT, "a staged step gave up waiting for its copies");
     if (status) return fail(h, LBM_ENONFINITE, "a step produced a non-finite or non-positive rho or T");
     return LBM_OK;
 }
@@ -564,6 +564,7 @@ int lbm_status(lbm_handle h)
                                     cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "status readback");
+    if (status & 2) return LBM_ETIMEOUT;
     return status ? LBM_ENONFINITE : LBM_OK;
 }
 

@@ -86,6 +86,13 @@ ONE_STEP = [
     ("D2Q49", (129, 2), ("copy", "copy"), "stream", 0),
     ("D2Q49", (17, 11), ("periodic", "copy"), "fd", 5),
     ("D2Q49", (7, 1), ("periodic", "periodic"), "stream", 3),
+    # widths that are multiples of 4 take the TMA-staged STREAM kernel:
+    # ragged last tile, a grid narrower than the staged halo, copy ends
+    ("D2Q49", (132, 5), ("periodic", "periodic"), "stream", 3),
+    ("D2Q37", (8, 3), ("copy", "periodic"), "stream", 3),
+    ("D1Q7", (4,), ("copy",), "stream", 4),
+    ("D1Q7", (12,), ("periodic",), "stream", 2),
+    ("D2Q49", (260, 2), ("copy", "copy"), "stream", 0),
 ]
 
 
