@@ -178,6 +178,73 @@ int64_t lbm_launch_count(lbm_handle h);
 
 void lbm_destroy(lbm_handle h);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles of independent 1-D problems in one persistent launch.
+ *
+ * `count` shock tubes (or any 1-D problems), each on D1Q7 + D1Q7 (Table II)
+ * with copy (zero-gradient) ends, each with its own length L_k, rotational
+ * degrees n_k (gamma_k = (3+n_k)/(1+n_k), Sec. III) and relaxation time
+ * tau_k, all advanced by the same step as lbm_step (Sec. V; STREAM or FD
+ * transport, one mode per ensemble) and giving bit-identical results to
+ * running each problem through its own lbm_handle.  One launch advances every
+ * problem by k steps: blocks stay resident and claim whole problems, longest
+ * first, through an atomic counter; each block runs all k steps of its
+ * problem with a block barrier between steps, so a problem's state stays in
+ * L2 while it is worked on.  The launch (counter reset + kernel) is built
+ * once as a CUDA graph and replayed.  Every problem carries 7 rotational
+ * populations (with n_k = 0 they carry no energy).
+ *
+ * Layout.  Macro fields are float32 device arrays of total_nodes = sum L_k
+ * entries, problem k at node offset sum_{j<k} L_j (u has one component).
+ * The state buffers hold, for problem k, 14 arrays of roundup(L_k, 32)
+ * floats.  As for lbm_handle, the caller allocates two state buffers and a
+ * work buffer (per-problem table, per-problem status words, the counter) of
+ * the reported sizes, 256-byte aligned; the library allocates no device
+ * memory.  Status: a non-finite or non-positive rho or T in problem k sets
+ * bit 0 of its status word; lbm_batch_status reads them. */
+typedef struct lbm_batch_ctx *lbm_batch;
+
+/* count >= 1; lengths[k] >= 1; n[k] >= 0; tau[k] > 0 (host arrays, copied);
+ * mode LBM_MODE_STREAM or LBM_MODE_FD with m_fd >= 1 (Eq. DisEvolSpaTiI).
+ * The state must stay below 2^31 floats (LBM_ESIZE otherwise). */
+int lbm_batch_create(int count, const int64_t *lengths, const int *n, const double *tau,
+                     int mode, int m_fd, lbm_batch *out);
+
+/* Bytes for each state buffer and for the work buffer; total node count. */
+int lbm_batch_sizes(lbm_batch b, size_t *state_bytes, size_t *work_bytes, int64_t *total_nodes);
+
+/* Bind caller memory and the stream; uploads the per-problem table
+ * (asynchronously, from host memory owned by the handle). */
+int lbm_batch_bind(lbm_batch b, void *buf_a, void *buf_b, size_t state_bytes, void *work,
+                   size_t work_bytes, void *stream);
+
+/* Equilibrium initial state of every problem (as lbm_set_macro); clears
+ * the status words.  Asynchronous. */
+int lbm_batch_set_macro(lbm_batch b, const float *rho, const float *u, const float *T);
+
+/* Advance every problem by k >= 0 steps in one persistent launch.
+ * Asynchronous. */
+int lbm_batch_run(lbm_batch b, int64_t k);
+
+/* rho, u, T of every problem (layout above).  Asynchronous. */
+int lbm_batch_get_moments(lbm_batch b, float *rho, float *u, float *T);
+
+/* Per-problem status words into a HOST array of `count` ints (may be NULL)
+ * and the number of problems whose word is non-zero.  Synchronizing. */
+int lbm_batch_status(lbm_batch b, int *status, int *n_bad);
+
+/* Threads per block of the persistent launch: lbm_batch_set_block sets it
+ * (32..1024, a multiple of 32); lbm_batch_autotune times `sample_steps`
+ * steps of the bound ensemble for each of 128, 256, 512 and 1024 threads
+ * with resident-block grids and keeps the fastest (returned in *threads).
+ * Autotuning advances the state: call lbm_batch_set_macro afterwards. */
+int lbm_batch_set_block(lbm_batch b, int threads);
+int lbm_batch_autotune(lbm_batch b, int64_t sample_steps, int *threads);
+
+int64_t lbm_batch_launch_count(lbm_batch b);
+const char *lbm_batch_last_error(lbm_batch b);
+void lbm_batch_destroy(lbm_batch b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,4 +5,4 @@ from ``csrc/``) that advances the translational and rotational populations of
 Hu, Zhang & Geng's decoupled scheme (arXiv 1606.06107).  ``lbm`` is a thin
 ctypes binding over it; PyTorch supplies only device memory and streams.
 """
-from .lbm import Lbm, LbmError, load_library  # noqa: F401
+from .lbm import Lbm, LbmBatch, LbmError, load_library  # noqa: F401

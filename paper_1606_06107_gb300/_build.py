@@ -16,6 +16,11 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# The single-problem D1Q7 kernels and the ensemble kernels run the same node
+# update and must round identically: without multiply-add contraction the
+# arithmetic is fixed by the source (explicit fmaf only), not by how the
+# compiler schedules each kernel.
+PER_SOURCE = {"lbm_d1q7.cu": ["-fmad=false"], "lbm_batch.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -50,7 +55,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *PER_SOURCE.get(os.path.basename(src), []), *extra, "-c", src,
+               "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{res.stderr}")

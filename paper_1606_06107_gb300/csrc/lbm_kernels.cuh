@@ -184,10 +184,15 @@ __device__ __forceinline__ Offsets node_offsets(const Params<Q> &p, int x, int y
     return o;
 }
 
-template <int Q>
+// CG = false: read-only path (the source buffer is never written during the
+// launch).  CG = true: L2-coherent loads, for kernels that read back what
+// the same launch wrote (the persistent ensemble kernel).
+template <bool CG = false, int Q>
 __device__ __forceinline__ float ld(const Params<Q> &p, int pop, int off)
 {
-    return __ldg(p.src + ((uint32_t)pop * (uint32_t)p.S + (uint32_t)off));
+    const float *a = p.src + ((uint32_t)pop * (uint32_t)p.S + (uint32_t)off);
+    if constexpr (CG) return __ldcg(a);
+    return __ldg(a);
 }
 template <int Q>
 __device__ __forceinline__ void st(const Params<Q> &p, int pop, int off, float v)
@@ -361,7 +366,7 @@ __device__ __forceinline__ void heq_node(const Params<Q> &p, float T, float T_la
 // convection by u at Courant number u * nu_scale, BGK toward h^eq(T).
 // (Issuing these neighbour loads right after the moments, before the
 // translational work, measured 9 % slower on the 2048^2 workload.)
-template <int D, int Q>
+template <int D, bool CG = false, int Q>
 __device__ __forceinline__ void rot_advect(const Params<Q> &p, const Offsets &o,
                                            const float *h, const Moments &m, float *adv)
 {
@@ -379,7 +384,8 @@ __device__ __forceinline__ void rot_advect(const Params<Q> &p, const Offsets &o,
         const float anu = fabsf(nu[a]);
 #pragma unroll
         for (int j = 0; j < 7; ++j)
-            adv[j] += upwind_abs(anu, ld(p, Q + j, uu), ld(p, Q + j, u1), h[j], ld(p, Q + j, d1));
+            adv[j] += upwind_abs(anu, ld<CG>(p, Q + j, uu), ld<CG>(p, Q + j, u1), h[j],
+                                 ld<CG>(p, Q + j, d1));
     }
 }
 
@@ -398,7 +404,7 @@ __device__ __forceinline__ void rot_store(const Params<Q> &p, int self, const fl
 // Load the time-t populations of one node.  STREAM: pull g_i(x) = ft_i(x - e_i).
 // FD: g_i(x) = ft_i(x).
 
-template <int LAT, bool ROT, int MODE, int Q>
+template <int LAT, bool ROT, int MODE, bool CG = false, int Q>
 __device__ __forceinline__ void load_node(const Params<Q> &p, const Offsets &o, float *g,
                                           float *h)
 {
@@ -408,18 +414,18 @@ __device__ __forceinline__ void load_node(const Params<Q> &p, const Offsets &o, 
         const int off = (MODE == 0)
                             ? o.z[3 - L::ez(i)] + o.y[3 - L::ey(i)] + o.x[3 - L::ex(i)]
                             : o.self();
-        g[i] = ld(p, i, off);
+        g[i] = ld<CG>(p, i, off);
     }
     if (ROT) {
 #pragma unroll
-        for (int j = 0; j < 7; ++j) h[j] = ld(p, L::Q + j, o.self());
+        for (int j = 0; j < 7; ++j) h[j] = ld<CG>(p, L::Q + j, o.self());
     }
 }
 
 // FD transport of one translational population (Eq. DisEvolSpaTiI): the
 // upwind side of each axis is fixed by the sign of e_ia, the Courant number
 // is |e_ia| / m.
-template <int LAT, int I, int Q>
+template <int LAT, int I, bool CG = false, int Q>
 __device__ __forceinline__ float fd_convect(const Params<Q> &p, const Offsets &o, float g0)
 {
     using L = Lattice<LAT>;
@@ -432,17 +438,17 @@ __device__ __forceinline__ float fd_convect(const Params<Q> &p, const Offsets &o
         const int rest = o.self() - oa[3];
         const bool pos = e[a] > 0;
         const float anu = (float)(pos ? e[a] : -e[a]) * p.inv_m;
-        adv += upwind_abs(anu, ld(p, I, rest + (pos ? oa[1] : oa[5])),
-                          ld(p, I, rest + (pos ? oa[2] : oa[4])), g0,
-                          ld(p, I, rest + (pos ? oa[4] : oa[2])));
+        adv += upwind_abs(anu, ld<CG>(p, I, rest + (pos ? oa[1] : oa[5])),
+                          ld<CG>(p, I, rest + (pos ? oa[2] : oa[4])), g0,
+                          ld<CG>(p, I, rest + (pos ? oa[4] : oa[2])));
     }
     return adv;
 }
 
-template <int LAT, int MODE, int I, int Q>
+template <int LAT, int MODE, int I, bool CG = false, int Q>
 __device__ __forceinline__ float transport(const Params<Q> &p, const Offsets &o, float g0)
 {
-    if constexpr (MODE == 1) return fd_convect<LAT, I>(p, o, g0);
+    if constexpr (MODE == 1) return fd_convect<LAT, I, CG>(p, o, g0);
     return 0.f;
 }
 
@@ -568,12 +574,9 @@ __global__ void LBM_STEP_BOUNDS k_step(const Params<Lattice<LAT>::Q> p)
 // Initial state at equilibrium (pull pre-image in STREAM mode).
 
 template <int LAT, bool ROT, int MODE>
-__global__ void __launch_bounds__(kBlockX) k_init(const Params<Lattice<LAT>::Q> p)
+__device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q> &p, int x, int y, int z)
 {
     using L = Lattice<LAT>;
-    const int x = blockIdx.x * kBlockX + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= p.X) return;
     const int self = (z * p.Y + y) * p.pitch + x;
     const float *rho_in = p.in0, *u_in = p.in1, *T_in = p.in2;
 #pragma unroll 1
@@ -606,19 +609,24 @@ __global__ void __launch_bounds__(kBlockX) k_init(const Params<Lattice<LAT>::Q> 
     }
 }
 
+template <int LAT, bool ROT, int MODE>
+__global__ void __launch_bounds__(kBlockX) k_init(const Params<Lattice<LAT>::Q> p)
+{
+    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    if (x >= p.X) return;
+    init_node<LAT, ROT, MODE>(p, x, blockIdx.y, blockIdx.z);
+}
+
 // ---------------------------------------------------------------------------
 // rho, u, T of the current state into unpadded caller arrays.
 
-template <int LAT, bool ROT, int MODE>
-__global__ void __launch_bounds__(kBlockX) k_moments(const Params<Lattice<LAT>::Q> p)
+template <int LAT, bool ROT, int MODE, bool CG = false>
+__device__ __forceinline__ void moments_node(const Params<Lattice<LAT>::Q> &p, int x, int y, int z)
 {
     using L = Lattice<LAT>;
-    const int x = blockIdx.x * kBlockX + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= p.X) return;
     const Offsets o = node_offsets<L::D>(p, x, y, z);
     float g[L::Q], h[7];
-    load_node<LAT, ROT, MODE>(p, o, g, h);
+    load_node<LAT, ROT, MODE, CG>(p, o, g, h);
     const Moments m = node_moments<LAT, ROT>(p, g, h);
     const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
     p.out0[node] = m.rho;
@@ -626,6 +634,14 @@ __global__ void __launch_bounds__(kBlockX) k_moments(const Params<Lattice<LAT>::
     if (L::D >= 2) p.out1[p.N + node] = m.uy;
     if (L::D >= 3) p.out1[2 * p.N + node] = m.uz;
     p.out2[node] = m.T;
+}
+
+template <int LAT, bool ROT, int MODE>
+__global__ void __launch_bounds__(kBlockX) k_moments(const Params<Lattice<LAT>::Q> p)
+{
+    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    if (x >= p.X) return;
+    moments_node<LAT, ROT, MODE>(p, x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------

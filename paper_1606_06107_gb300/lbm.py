@@ -50,6 +50,24 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_double)]),
     "lbm_launch_count": (_i64, [_vp]),
     "lbm_destroy": (None, [_vp]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_i64),
+                                        ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(_vp)]),
+    "lbm_batch_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i64)]),
+    "lbm_batch_bind": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t,
+                                      _vp]),
+    "lbm_batch_set_macro": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_batch_run": (ctypes.c_int, [_vp, _i64]),
+    "lbm_batch_get_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_batch_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_set_block": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "lbm_batch_autotune": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_launch_count": (_i64, [_vp]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_batch_destroy": (None, [_vp]),
 }
 
 
@@ -225,6 +243,117 @@ class Lbm:
     def close(self):
         if getattr(self, "h", None) is not None:
             self.lib.lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LbmBatch:
+    """An ensemble of independent 1-D problems (D1Q7 + D1Q7, copy ends)
+    advanced together by one persistent launch (include/lbm.h, lbm_batch_*).
+
+    ``lengths``, ``n`` and ``tau`` give each problem's node count, rotational
+    degrees of freedom and relaxation time.  Macro fields are concatenated:
+    problem k occupies nodes ``offsets[k] : offsets[k] + lengths[k]``.
+    """
+
+    def __init__(self, lengths, n, tau, mode: str = "fd", m_fd: int = 10, device=None,
+                 stream=None):
+        import torch
+
+        self.torch = torch
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise LbmError(-3, "no CUDA device")
+        self.device = torch.device(device if device is not None else "cuda")
+        self.lengths = np.asarray(lengths, dtype=np.int64)
+        self.count = int(self.lengths.size)
+        self.offsets = np.concatenate([[0], np.cumsum(self.lengths)[:-1]]).astype(np.int64)
+        nn = np.ascontiguousarray(n, dtype=np.int32)
+        tt = np.ascontiguousarray(tau, dtype=np.float64)
+        L = np.ascontiguousarray(self.lengths)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            h = ctypes.c_void_p()
+            rc = self.lib.lbm_batch_create(
+                self.count, L.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                tt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), MODES[mode], int(m_fd),
+                ctypes.byref(h))
+            if rc != 0:
+                raise LbmError(rc, "lbm_batch_create")
+            self.h = h
+            sb, wb, tn = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int64()
+            self._check(self.lib.lbm_batch_sizes(h, ctypes.byref(sb), ctypes.byref(wb),
+                                                 ctypes.byref(tn)))
+            self.state_bytes, self.work_bytes, self.N = sb.value, wb.value, tn.value
+            self.buf_a = torch.empty(self.state_bytes, dtype=torch.uint8, device=self.device)
+            self.buf_b = torch.empty(self.state_bytes, dtype=torch.uint8, device=self.device)
+            self.work = torch.zeros(self.work_bytes, dtype=torch.uint8, device=self.device)
+            self._check(self.lib.lbm_batch_bind(h, self.buf_a.data_ptr(), self.buf_b.data_ptr(),
+                                                self.state_bytes, self.work.data_ptr(),
+                                                self.work_bytes, self.stream.cuda_stream))
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise LbmError(rc, self.lib.lbm_batch_last_error(self.h).decode())
+
+    def _field(self, a):
+        t = self.torch
+        x = t.as_tensor(a, device=self.device, dtype=t.float32).reshape(-1).contiguous()
+        if x.numel() != self.N:
+            raise LbmError(-1, "field has the wrong number of entries")
+        return x
+
+    def set_macro(self, rho, u, T):
+        with self.torch.cuda.device(self.device):
+            r, uu, tt = self._field(rho), self._field(u), self._field(T)
+            self._keep = (r, uu, tt)
+            self._check(self.lib.lbm_batch_set_macro(self.h, r.data_ptr(), uu.data_ptr(),
+                                                     tt.data_ptr()))
+
+    def run(self, k: int):
+        with self.torch.cuda.device(self.device):
+            self._check(self.lib.lbm_batch_run(self.h, int(k)))
+
+    def moments(self):
+        t = self.torch
+        with t.cuda.device(self.device):
+            rho = t.empty(self.N, dtype=t.float32, device=self.device)
+            u = t.empty(self.N, dtype=t.float32, device=self.device)
+            T = t.empty(self.N, dtype=t.float32, device=self.device)
+            self._check(self.lib.lbm_batch_get_moments(self.h, rho.data_ptr(), u.data_ptr(),
+                                                       T.data_ptr()))
+            return rho, u, T
+
+    def status(self):
+        """(per-problem status words, number of problems flagged)."""
+        st = (ctypes.c_int * self.count)()
+        bad = ctypes.c_int()
+        with self.torch.cuda.device(self.device):
+            self._check(self.lib.lbm_batch_status(self.h, st, ctypes.byref(bad)))
+        return np.array(st[:]), bad.value
+
+    def set_block(self, threads: int):
+        self._check(self.lib.lbm_batch_set_block(self.h, int(threads)))
+
+    def autotune(self, sample_steps: int = 20) -> int:
+        out = ctypes.c_int()
+        with self.torch.cuda.device(self.device):
+            self._check(self.lib.lbm_batch_autotune(self.h, int(sample_steps), ctypes.byref(out)))
+        return out.value
+
+    @property
+    def launches(self) -> int:
+        return self.lib.lbm_batch_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self.lib.lbm_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

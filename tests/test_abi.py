@@ -92,3 +92,25 @@ def test_product_path_has_no_oracle_dependency():
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 assert not pat.search(open(os.path.join(root, f)).read()), f
+
+
+def test_batch_create_validation_and_sizes(lbmlib):
+    L = (ctypes.c_int64 * 3)(10, 40, 33)
+    n = (ctypes.c_int * 3)(2, 4, 0)
+    tau = (ctypes.c_double * 3)(0.7, 0.6, 1.0)
+    h = ctypes.c_void_p()
+    assert lbmlib.lbm_batch_create(0, L, n, tau, 1, 10, ctypes.byref(h)) == -1
+    assert lbmlib.lbm_batch_create(3, L, n, tau, 1, 0, ctypes.byref(h)) == -1
+    bad_tau = (ctypes.c_double * 3)(0.7, -1.0, 1.0)
+    assert lbmlib.lbm_batch_create(3, L, n, bad_tau, 1, 10, ctypes.byref(h)) == -1
+    assert lbmlib.lbm_batch_create(3, L, n, tau, 1, 10, ctypes.byref(h)) == 0
+    try:
+        sb, wb, tn = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int64()
+        assert lbmlib.lbm_batch_sizes(h, ctypes.byref(sb), ctypes.byref(wb), ctypes.byref(tn)) == 0
+        assert tn.value == 83
+        assert sb.value == 4 * 14 * (32 + 64 + 64)  # each problem padded to 32 floats
+        assert lbmlib.lbm_batch_run(h, 1) == -6      # no state yet
+        assert lbmlib.lbm_batch_set_block(h, 100) == -1
+        assert lbmlib.lbm_batch_set_block(h, 512) == 0
+    finally:
+        lbmlib.lbm_batch_destroy(h)

@@ -1,0 +1,118 @@
+"""The ensemble path (lbm_batch_*): one persistent launch advancing many
+independent 1-D problems gives bit-identical results to running each problem
+through its own lbm_handle, and agrees with the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_1606_06107_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def tubes(specs, seed=0):
+    """Two-state tubes: (length, n, tau, left (rho,u,p), right (rho,u,p))."""
+    rho, u, T = [], [], []
+    for L, n, tau, left, right in specs:
+        r, uu, t = workloads._two_state_1d(L, left, right)
+        rho.append(r), u.append(uu), T.append(t)
+    return (np.concatenate(rho), np.concatenate(u), np.concatenate(T))
+
+
+SPECS = [
+    (1, 2, 0.7, (1.0, 0.0, 1.0), (1.0, 0.0, 1.0)),
+    (7, 4, 2 / 3, (1.0, 0.0, 1.0), (0.8, 0.0, 0.7)),
+    (130, 0, 0.6, (1.0, 0.1, 1.0), (0.9, 0.0, 0.8)),
+    (257, 6, 0.9, (1.0, 0.0, 1.0), (0.7, 0.0, 0.6)),
+    (1000, 4, 2 / 3, (1.0, 0.0, 1.0), (0.5, 0.0, 0.4)),
+    (64, 7, 0.55, (1.1, -0.05, 1.0), (1.0, 0.0, 0.9)),
+]
+
+
+def plain_run(spec, rho, u, T, mode, m_fd, steps):
+    from paper_1606_06107_gb300 import Lbm
+    L, n, tau = spec[:3]
+    s = Lbm("D1Q7", n, tau, (L,), ("copy",), mode=mode, m_fd=m_fd)
+    s.set_macro(rho, u[None], T)
+    s.step(steps)
+    return [x.cpu().numpy().reshape(-1) for x in s.moments()]
+
+
+@pytest.mark.parametrize("mode,m_fd", [("fd", 10), ("stream", 1)])
+def test_batch_bitwise_equals_single_runs(mode, m_fd):
+    from paper_1606_06107_gb300 import LbmBatch
+    rho, u, T = tubes(SPECS)
+    b = LbmBatch([s[0] for s in SPECS], [s[1] for s in SPECS], [s[2] for s in SPECS],
+                 mode=mode, m_fd=m_fd)
+    b.set_macro(rho, u, T)
+    b.run(20)
+    b.run(31)          # odd split: the state changes buffers between calls
+    got = [x.cpu().numpy() for x in b.moments()]
+    st, bad = b.status()
+    assert bad == 0
+    for k, spec in enumerate(SPECS):
+        sl = slice(b.offsets[k], b.offsets[k] + spec[0])
+        ref = plain_run(spec, rho[sl], u[sl], T[sl], mode, m_fd, 51)
+        for a, r in zip(got, ref):
+            assert np.array_equal(a[sl], r), (k, np.abs(a[sl] - r).max())
+
+
+def test_batch_matches_oracle(orc):
+    """Two tubes, FD transport (m = 10), 1000 steps: rel-L1 <= 1e-5."""
+    from paper_1606_06107_gb300 import LbmBatch
+    specs = [SPECS[4], (600, 2, 0.8, (1.0, 0.0, 1.0), (0.6, 0.0, 0.5))]
+    rho, u, T = tubes(specs)
+    b = LbmBatch([s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs], mode="fd",
+                 m_fd=10)
+    b.set_macro(rho, u, T)
+    b.run(1000)
+    got = [x.cpu().numpy().astype(np.float64) for x in b.moments()]
+    for k, (L, n, tau, _, _) in enumerate(specs):
+        sl = slice(b.offsets[k], b.offsets[k] + L)
+        ref = orc.Sim(orc.D1Q7, n, tau, (L,), (orc.COPY,), mode=orc.FD, m_fd=10)
+        ref.set_macro(rho[sl], u[sl][None], T[sl])
+        ref.step(1000)
+        for a, r in zip(got, ref.moments()):
+            r = np.asarray(r).reshape(-1)
+            assert np.abs(a[sl] - r).sum() / np.abs(r).sum() <= 1e-5
+
+
+def test_batch_status_flags_only_the_bad_problem():
+    from paper_1606_06107_gb300 import LbmBatch
+    rho, u, T = tubes(SPECS)
+    T = T.copy()
+    k = 3
+    T[int(np.sum([s[0] for s in SPECS[:k]])) + 5] = -1.0
+    b = LbmBatch([s[0] for s in SPECS], [s[1] for s in SPECS], [s[2] for s in SPECS])
+    b.set_macro(rho, u, T)
+    b.run(3)
+    st, bad = b.status()
+    assert bad == 1 and st[k] != 0
+
+
+def test_autotune_then_rerun_is_unchanged():
+    from paper_1606_06107_gb300 import LbmBatch
+    rho, u, T = tubes(SPECS)
+    b = LbmBatch([s[0] for s in SPECS], [s[1] for s in SPECS], [s[2] for s in SPECS])
+    b.set_macro(rho, u, T)
+    b.run(10)
+    first = [x.cpu().numpy() for x in b.moments()]
+    threads = b.autotune(5)
+    assert threads in (128, 256, 512, 1024)
+    b.set_macro(rho, u, T)
+    b.run(10)
+    second = [x.cpu().numpy() for x in b.moments()]
+    assert all(np.array_equal(x, y) for x, y in zip(first, second))
+
+
+def test_ensemble_workload_generator_runs():
+    """A 64-tube slice of the ensemble workload (uneven lengths, gamma and
+    tau per tube, pressure ratios up to 100) runs; the stable fraction is
+    reported by the status words, not asserted."""
+    from paper_1606_06107_gb300 import LbmBatch
+    wls = workloads.batched_tubes(count=64, seed=1, lmax=2048)
+    b = LbmBatch([w.shape[0] for w in wls], [w.n for w in wls], [w.tau for w in wls])
+    b.set_macro(np.concatenate([w.rho for w in wls]), np.concatenate([w.u[0] for w in wls]),
+                np.concatenate([w.T for w in wls]))
+    b.run(100)
+    st, bad = b.status()
+    assert st.shape == (64,) and 0 <= bad <= 64
