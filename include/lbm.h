@@ -91,6 +91,16 @@ int lbm_create(int D, int lattice, int n, double tau, lbm_handle *out);
  * Must be called before lbm_set_grid. */
 int lbm_set_mode(lbm_handle h, int mode, int m_fd);
 
+/* Storage of the populations in HBM (before lbm_set_grid).  LBM_STORE_F32
+ * (default) keeps float32 values.  LBM_STORE_F16 / LBM_STORE_BF16 keep the
+ * relative deviation from the rest equilibrium, d_i = f_i / w_i - 1, as IEEE
+ * half / bfloat16, halving the bytes per step; all arithmetic stays float32
+ * and the temperature is recovered from the total energy in double
+ * precision (Eq. T).  The reduced precision changes results by the storage
+ * rounding (about 2^-11 resp. 2^-8 of d_i per step). */
+enum lbm_storage { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2 };
+int lbm_set_storage(lbm_handle h, int storage);
+
 /* Set the grid: shape[0..D-1] = X (fastest), Y, Z, each >= 1 (Y, Z <= 65535);
  * bc[0..D-1] per-axis boundary (periodic wrap, or copy = zero-gradient
  * clamp to the edge node, the paper's "open" boundary of Sec. VI).  Returns

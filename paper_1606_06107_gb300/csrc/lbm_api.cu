@@ -20,6 +20,7 @@ using lbm::Op;
 struct lbm_ctx {
     int D = 0, lattice = 0, n = 0, Q = 0, Qr = 0;
     int mode = LBM_MODE_STREAM, m_fd = 1;
+    int storage = LBM_STORE_F32;
     double tau = 0.0;
     double r = 0.0;
     double w[lbm::kMaxQ] = {};
@@ -239,6 +240,7 @@ Args make_args(const lbm_ctx *h)
     a.Qr = h->Qr;
     a.mode = h->mode;
     a.m_fd = h->m_fd;
+    a.storage = h->storage;
     a.X = (int)h->shape[0];
     a.Y = (int)h->shape[1];
     a.Z = (int)h->shape[2];
@@ -359,6 +361,16 @@ int lbm_create(int D, int lattice, int n, double tau, lbm_handle *out)
     return LBM_OK;
 }
 
+int lbm_set_storage(lbm_handle h, int storage)
+{
+    if (!h) return LBM_EINVAL;
+    if (h->grid_set) return fail(h, LBM_ESTATE, "lbm_set_storage must precede lbm_set_grid");
+    if (storage != LBM_STORE_F32 && storage != LBM_STORE_F16 && storage != LBM_STORE_BF16)
+        return fail(h, LBM_EINVAL, "unknown storage");
+    h->storage = storage;
+    return LBM_OK;
+}
+
 int lbm_set_mode(lbm_handle h, int mode, int m_fd)
 {
     if (!h) return LBM_EINVAL;
@@ -386,7 +398,9 @@ int lbm_set_grid(lbm_handle h, const int64_t *shape, const int *bc, size_t *stat
     }
     if (s[0] > (int64_t)1 << 30 || s[1] > 65535 || s[2] > 65535)
         return fail(h, LBM_ESIZE, "X <= 2^30 and Y, Z <= 65535 are required");
-    const int64_t pitch = (s[0] + 31) / 32 * 32;
+    const size_t elem = (h->storage == LBM_STORE_F32) ? sizeof(float) : 2;
+    const int64_t row_align = 128 / (int64_t)elem;  // rows start on 128-byte lines
+    const int64_t pitch = (s[0] + row_align - 1) / row_align * row_align;
     const int64_t S = pitch * s[1] * s[2];
     // the kernels index the whole state buffer with 32-bit element offsets
     if (S * (h->Q + h->Qr) > 0x7fffffffLL)
@@ -398,7 +412,7 @@ int lbm_set_grid(lbm_handle h, const int64_t *shape, const int *bc, size_t *stat
     h->pitch = (int)pitch;
     h->S = S;
     h->N = s[0] * s[1] * s[2];
-    h->state_bytes = sizeof(float) * (size_t)(h->Q + h->Qr) * (size_t)S;
+    h->state_bytes = elem * (size_t)(h->Q + h->Qr) * (size_t)S;
     h->work_bytes = lbm::kWorkBytes;
     h->grid_set = true;
     if (state_bytes) *state_bytes = h->state_bytes;

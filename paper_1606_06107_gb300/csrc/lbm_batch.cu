@@ -17,7 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
-#include "lbm_kernels.cuh"
+#include "lbm_step.cuh"
 
 namespace lbm {
 namespace {

@@ -22,6 +22,7 @@ enum class Op { Step, Init, Moments, Conserve, GetState, SetState };
 // Everything a kernel launch needs; filled by the host API.
 struct Args {
     int lattice, D, Q, Qr, mode, m_fd;
+    int storage;  // lbm_storage: 0 float, 1 half deviations, 2 bfloat16 deviations
     int X, Y, Z, pitch;
     int64_t S;  // population stride in floats (pitch * Y * Z)
     int64_t N;  // nodes (X * Y * Z)
@@ -29,8 +30,8 @@ struct Args {
     float r, omega, nu_scale, cT, half_n, half_n_r2, inv_m;
     float w[kMaxQ];
     float wr[7];
-    const float *src;  // current state (Step reads, Moments/Conserve/GetState read)
-    float *dst;        // next state (Step writes, Init/SetState write)
+    const void *src;  // current state (Step reads, Moments/Conserve/GetState read)
+    void *dst;        // next state (Step writes, Init/SetState write)
     const float *in0, *in1, *in2;  // Init: rho, u, T; SetState: ft, fr
     float *out0, *out1, *out2;     // Moments: rho, u, T; GetState: ft, fr
     int *status;

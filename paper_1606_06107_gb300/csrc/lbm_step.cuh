@@ -10,11 +10,15 @@
 // address is one 3-input add plus one wide multiply-add.
 //
 // The step is memory bound: every population is read once and written once
-// per step; all moments and equilibria live in registers.  One thread owns
+// per step; all moments and equilibria live in registers.  Populations are
+// stored as float, or as __half / __nv_bfloat16 deviations (Storage below);
+// every kernel is instantiated per storage type.  One thread owns
 // one node; a block is 128 consecutive x positions of one row.
 #pragma once
 #include <cstdint>
 #include <type_traits>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lbm_internal.h"
@@ -104,12 +108,35 @@ template <int LAT> __host__ __device__ constexpr int e2_of(int i)
 }
 
 // ---------------------------------------------------------------------------
+// Population storage.  float: the value itself.  __half / __nv_bfloat16: the
+// relative deviation from the rest equilibrium, d_i = f_i / w_i - 1 (the
+// equilibrium at rho = 1, u = 0, T = 1 has d_i = 0), so the 11 (8) mantissa
+// bits resolve the departure from rest rather than the weight's magnitude.
+// All arithmetic stays float32; a value is decoded on load and encoded on
+// store.
+template <typename ST> struct Storage;
+template <> struct Storage<__half> {
+    __device__ static float decode(__half v, float w) { return fmaf(w, __half2float(v), w); }
+    __device__ static __half encode(float f, float inv_w) { return __float2half_rn(fmaf(f, inv_w, -1.0f)); }
+};
+template <> struct Storage<__nv_bfloat16> {
+    __device__ static float decode(__nv_bfloat16 v, float w)
+    {
+        return fmaf(w, __bfloat162float(v), w);
+    }
+    __device__ static __nv_bfloat16 encode(float f, float inv_w)
+    {
+        return __float2bfloat16_rn(fmaf(f, inv_w, -1.0f));
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Kernel parameters (passed by value: they live in the constant bank, so the
 // per-population weights become constant operands of the FMAs).
 
-template <int Q> struct Params {
-    const float *__restrict__ src;
-    float *__restrict__ dst;
+template <int Q, typename ST = float> struct Params {
+    const ST *__restrict__ src;  // state, in the storage type
+    ST *__restrict__ dst;
     const float *in0, *in1, *in2;
     float *out0, *out1, *out2;
     int *status;
@@ -118,15 +145,15 @@ template <int Q> struct Params {
     int X, Y, Z, pitch;
     int bc0, bc1, bc2;
     float r, r2, inv_r2, omega, nu_scale, cT, half_n, half_n_r2, inv_m;
-    float w[Q];
-    float wr[7];
+    float w[Q], iw[Q];    // weights and their inverses (deviation storage)
+    float wr[7], iwr[7];
 };
 
-template <int Q> Params<Q> make_params(const Args &a)
+template <int Q, typename ST = float> Params<Q, ST> make_params(const Args &a)
 {
-    Params<Q> p;
-    p.src = a.src;
-    p.dst = a.dst;
+    Params<Q, ST> p;
+    p.src = static_cast<const ST *>(a.src);
+    p.dst = static_cast<ST *>(a.dst);
     p.in0 = a.in0; p.in1 = a.in1; p.in2 = a.in2;
     p.out0 = a.out0; p.out1 = a.out1; p.out2 = a.out2;
     p.status = a.status;
@@ -144,8 +171,14 @@ template <int Q> Params<Q> make_params(const Args &a)
     p.half_n_r2 = a.half_n_r2;
     p.half_n = a.half_n;
     p.inv_m = a.inv_m;
-    for (int i = 0; i < Q; ++i) p.w[i] = a.w[i];
-    for (int j = 0; j < 7; ++j) p.wr[j] = a.wr[j];
+    for (int i = 0; i < Q; ++i) {
+        p.w[i] = a.w[i];
+        p.iw[i] = 1.0f / a.w[i];
+    }
+    for (int j = 0; j < 7; ++j) {
+        p.wr[j] = a.wr[j];
+        p.iwr[j] = 1.0f / a.wr[j];
+    }
     return p;
 }
 
@@ -171,8 +204,8 @@ struct Offsets {
     __device__ __forceinline__ int self() const { return z[3] + y[3] + x[3]; }
 };
 
-template <int D, int Q>
-__device__ __forceinline__ Offsets node_offsets(const Params<Q> &p, int x, int y, int z)
+template <int D, int Q, typename ST>
+__device__ __forceinline__ Offsets node_offsets(const Params<Q, ST> &p, int x, int y, int z)
 {
     Offsets o;
 #pragma unroll
@@ -187,17 +220,22 @@ __device__ __forceinline__ Offsets node_offsets(const Params<Q> &p, int x, int y
 // CG = false: read-only path (the source buffer is never written during the
 // launch).  CG = true: L2-coherent loads, for kernels that read back what
 // the same launch wrote (the persistent ensemble kernel).
-template <bool CG = false, int Q>
-__device__ __forceinline__ float ld(const Params<Q> &p, int pop, int off)
+template <bool CG = false, int Q, typename ST>
+__device__ __forceinline__ float ld(const Params<Q, ST> &p, int pop, int off)
 {
-    const float *a = p.src + ((uint32_t)pop * (uint32_t)p.S + (uint32_t)off);
-    if constexpr (CG) return __ldcg(a);
-    return __ldg(a);
+    const ST *a = p.src + ((uint32_t)pop * (uint32_t)p.S + (uint32_t)off);
+    ST v;
+    if constexpr (CG) v = __ldcg(a);
+    else v = __ldg(a);
+    if constexpr (std::is_same<ST, float>::value) return v;
+    else return Storage<ST>::decode(v, pop < Q ? p.w[pop] : p.wr[pop - Q]);
 }
-template <int Q>
-__device__ __forceinline__ void st(const Params<Q> &p, int pop, int off, float v)
+template <int Q, typename ST>
+__device__ __forceinline__ void st(const Params<Q, ST> &p, int pop, int off, float v)
 {
-    p.dst[(uint32_t)pop * (uint32_t)p.S + (uint32_t)off] = v;
+    ST *a = p.dst + ((uint32_t)pop * (uint32_t)p.S + (uint32_t)off);
+    if constexpr (std::is_same<ST, float>::value) *a = v;
+    else *a = Storage<ST>::encode(v, pop < Q ? p.iw[pop] : p.iwr[pop - Q]);
 }
 
 // ---------------------------------------------------------------------------
@@ -212,8 +250,8 @@ struct Moments {
     float j[3], T_lat, E2_eq;
 };
 
-template <int LAT, bool ROT, int Q>
-__device__ __forceinline__ Moments node_moments(const Params<Q> &p, const float *g,
+template <int LAT, bool ROT, int Q, typename ST>
+__device__ __forceinline__ Moments node_moments(const Params<Q, ST> &p, const float *g,
                                                 const float *h)
 {
     using L = Lattice<LAT>;
@@ -269,7 +307,16 @@ __device__ __forceinline__ Moments node_moments(const Params<Q> &p, const float 
     // exactly: a rounded 2/(D+n) (0.4f for D+n = 5) would bias T, and with it
     // the total energy, by the same ~1e-8 every step.
     const float jj = (jx * jx + jy * jy + jz * jz) * inv_rho;  // rho u^2 / r^2
-    m.T_lat = __fdiv_rn(0.5f * (e2 - jj) * inv_rho + (ROT ? p.half_n * R2 : 0.f), p.cT);
+    if constexpr (sizeof(ST) < sizeof(float)) {
+        // reduced-precision storage: the temperature is recovered from the
+        // total energy in double precision (e2 - jj cancels at high Mach)
+        const double rd = (double)rho;
+        const double jjd = ((double)jx * jx + (double)jy * jy + (double)jz * jz) / rd;
+        const double num = 0.5 * ((double)e2 - jjd) / rd + (ROT ? (double)p.half_n * R2 : 0.0);
+        m.T_lat = (float)(num / (double)p.cT);
+    } else {
+        m.T_lat = __fdiv_rn(0.5f * (e2 - jj) * inv_rho + (ROT ? p.half_n * R2 : 0.f), p.cT);
+    }
     m.T = p.r2 * m.T_lat;
     m.E2_eq = jj + (float)L::D * rho * m.T_lat;  // rho (u^2 + D T) / r^2
     return m;
@@ -343,8 +390,8 @@ __device__ __forceinline__ float upwind_abs(float anu, float fuu, float fu, floa
 // drift that would accumulate; the defects are put back on the j = 3 (rest)
 // and j = 2, 4 (+-r) entries, which leaves the odd moments untouched.  In
 // exact arithmetic both corrections are zero.
-template <int Q>
-__device__ __forceinline__ void heq_node(const Params<Q> &p, float T, float T_lat, float *heq)
+template <int Q, typename ST>
+__device__ __forceinline__ void heq_node(const Params<Q, ST> &p, float T, float T_lat, float *heq)
 {
     const float t = T - 1.0f;
     float m0 = 0.f, m2 = 0.f;
@@ -366,8 +413,8 @@ __device__ __forceinline__ void heq_node(const Params<Q> &p, float T, float T_la
 // convection by u at Courant number u * nu_scale, BGK toward h^eq(T).
 // (Issuing these neighbour loads right after the moments, before the
 // translational work, measured 9 % slower on the 2048^2 workload.)
-template <int D, bool CG = false, int Q>
-__device__ __forceinline__ void rot_advect(const Params<Q> &p, const Offsets &o,
+template <int D, bool CG = false, int Q, typename ST>
+__device__ __forceinline__ void rot_advect(const Params<Q, ST> &p, const Offsets &o,
                                            const float *h, const Moments &m, float *adv)
 {
 #pragma unroll
@@ -389,8 +436,8 @@ __device__ __forceinline__ void rot_advect(const Params<Q> &p, const Offsets &o,
     }
 }
 
-template <int Q>
-__device__ __forceinline__ void rot_store(const Params<Q> &p, int self, const float *h,
+template <int Q, typename ST>
+__device__ __forceinline__ void rot_store(const Params<Q, ST> &p, int self, const float *h,
                                           const Moments &m, const float *adv)
 {
     float heq[7];
@@ -404,8 +451,8 @@ __device__ __forceinline__ void rot_store(const Params<Q> &p, int self, const fl
 // Load the time-t populations of one node.  STREAM: pull g_i(x) = ft_i(x - e_i).
 // FD: g_i(x) = ft_i(x).
 
-template <int LAT, bool ROT, int MODE, bool CG = false, int Q>
-__device__ __forceinline__ void load_node(const Params<Q> &p, const Offsets &o, float *g,
+template <int LAT, bool ROT, int MODE, bool CG = false, int Q, typename ST>
+__device__ __forceinline__ void load_node(const Params<Q, ST> &p, const Offsets &o, float *g,
                                           float *h)
 {
     using L = Lattice<LAT>;
@@ -425,8 +472,8 @@ __device__ __forceinline__ void load_node(const Params<Q> &p, const Offsets &o, 
 // FD transport of one translational population (Eq. DisEvolSpaTiI): the
 // upwind side of each axis is fixed by the sign of e_ia, the Courant number
 // is |e_ia| / m.
-template <int LAT, int I, bool CG = false, int Q>
-__device__ __forceinline__ float fd_convect(const Params<Q> &p, const Offsets &o, float g0)
+template <int LAT, int I, bool CG = false, int Q, typename ST>
+__device__ __forceinline__ float fd_convect(const Params<Q, ST> &p, const Offsets &o, float g0)
 {
     using L = Lattice<LAT>;
     float adv = 0.f;
@@ -445,8 +492,8 @@ __device__ __forceinline__ float fd_convect(const Params<Q> &p, const Offsets &o
     return adv;
 }
 
-template <int LAT, int MODE, int I, bool CG = false, int Q>
-__device__ __forceinline__ float transport(const Params<Q> &p, const Offsets &o, float g0)
+template <int LAT, int MODE, int I, bool CG = false, int Q, typename ST>
+__device__ __forceinline__ float transport(const Params<Q, ST> &p, const Offsets &o, float g0)
 {
     if constexpr (MODE == 1) return fd_convect<LAT, I, CG>(p, o, g0);
     return 0.f;
@@ -479,8 +526,8 @@ template <int I, int N, typename F> __device__ __forceinline__ void static_for(F
 // (Eq. DisEvolI's BGK term, with the float32 corrections described above).
 // `tr(I, g_I)` returns the transport term of population I (zero in STREAM
 // mode, the upwind convection in FD mode).
-template <int LAT, typename Tr>
-__device__ __forceinline__ void collide_store(const Params<Lattice<LAT>::Q> &p, int self,
+template <int LAT, typename ST, typename Tr>
+__device__ __forceinline__ void collide_store(const Params<Lattice<LAT>::Q, ST> &p, int self,
                                               const float *g, const Moments &m, Tr &&tr)
 {
     using L = Lattice<LAT>;
@@ -546,8 +593,8 @@ __device__ __forceinline__ void collide_store(const Params<Lattice<LAT>::Q> &p, 
 // cp.async.bulk + an mbarrier ran 27 % slower -- blocks idle while their
 // copies land and the smem per block halves the resident warps -- and
 // cp.async.bulk.prefetch.L2 of rows 16..128 ahead ran 4..27 % slower.)
-template <int LAT, bool ROT, int MODE>
-__global__ void LBM_STEP_BOUNDS k_step(const Params<Lattice<LAT>::Q> p)
+template <int LAT, bool ROT, int MODE, typename ST>
+__global__ void LBM_STEP_BOUNDS k_step(const Params<Lattice<LAT>::Q, ST> p)
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
@@ -573,8 +620,8 @@ __global__ void LBM_STEP_BOUNDS k_step(const Params<Lattice<LAT>::Q> p)
 // ---------------------------------------------------------------------------
 // Initial state at equilibrium (pull pre-image in STREAM mode).
 
-template <int LAT, bool ROT, int MODE>
-__device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q> &p, int x, int y, int z)
+template <int LAT, bool ROT, int MODE, typename ST>
+__device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q, ST> &p, int x, int y, int z)
 {
     using L = Lattice<LAT>;
     const int self = (z * p.Y + y) * p.pitch + x;
@@ -609,8 +656,8 @@ __device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q> &p, int 
     }
 }
 
-template <int LAT, bool ROT, int MODE>
-__global__ void __launch_bounds__(kBlockX) k_init(const Params<Lattice<LAT>::Q> p)
+template <int LAT, bool ROT, int MODE, typename ST>
+__global__ void __launch_bounds__(kBlockX) k_init(const Params<Lattice<LAT>::Q, ST> p)
 {
     const int x = blockIdx.x * kBlockX + threadIdx.x;
     if (x >= p.X) return;
@@ -620,8 +667,8 @@ __global__ void __launch_bounds__(kBlockX) k_init(const Params<Lattice<LAT>::Q> 
 // ---------------------------------------------------------------------------
 // rho, u, T of the current state into unpadded caller arrays.
 
-template <int LAT, bool ROT, int MODE, bool CG = false>
-__device__ __forceinline__ void moments_node(const Params<Lattice<LAT>::Q> &p, int x, int y, int z)
+template <int LAT, bool ROT, int MODE, bool CG = false, typename ST>
+__device__ __forceinline__ void moments_node(const Params<Lattice<LAT>::Q, ST> &p, int x, int y, int z)
 {
     using L = Lattice<LAT>;
     const Offsets o = node_offsets<L::D>(p, x, y, z);
@@ -636,8 +683,8 @@ __device__ __forceinline__ void moments_node(const Params<Lattice<LAT>::Q> &p, i
     p.out2[node] = m.T;
 }
 
-template <int LAT, bool ROT, int MODE>
-__global__ void __launch_bounds__(kBlockX) k_moments(const Params<Lattice<LAT>::Q> p)
+template <int LAT, bool ROT, int MODE, typename ST>
+__global__ void __launch_bounds__(kBlockX) k_moments(const Params<Lattice<LAT>::Q, ST> p)
 {
     const int x = blockIdx.x * kBlockX + threadIdx.x;
     if (x >= p.X) return;
@@ -661,8 +708,8 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-template <int LAT, bool ROT, int MODE>
-__global__ void __launch_bounds__(kRedThreads) k_conserve(const Params<Lattice<LAT>::Q> p)
+template <int LAT, bool ROT, int MODE, typename ST>
+__global__ void __launch_bounds__(kRedThreads) k_conserve(const Params<Lattice<LAT>::Q, ST> p)
 {
     using L = Lattice<LAT>;
     double acc[kRedSlots] = {0, 0, 0, 0, 0, 0, 0, 0};  // mass, j[3], energy, hdev
@@ -706,8 +753,8 @@ __global__ void __launch_bounds__(kRedThreads) k_conserve(const Params<Lattice<L
 // ---------------------------------------------------------------------------
 // Canonical (unpadded) <-> internal (padded) population copies.
 
-template <int LAT, bool ROT>
-__global__ void __launch_bounds__(kBlockX) k_get_state(const Params<Lattice<LAT>::Q> p)
+template <int LAT, bool ROT, typename ST>
+__global__ void __launch_bounds__(kBlockX) k_get_state(const Params<Lattice<LAT>::Q, ST> p)
 {
     using L = Lattice<LAT>;
     const int x = blockIdx.x * kBlockX + threadIdx.x;
@@ -720,8 +767,8 @@ __global__ void __launch_bounds__(kBlockX) k_get_state(const Params<Lattice<LAT>
         for (int j = 0; j < 7; ++j) p.out1[(int64_t)j * p.N + node] = ld(p, L::Q + j, self);
 }
 
-template <int LAT, bool ROT>
-__global__ void __launch_bounds__(kBlockX) k_set_state(const Params<Lattice<LAT>::Q> p)
+template <int LAT, bool ROT, typename ST>
+__global__ void __launch_bounds__(kBlockX) k_set_state(const Params<Lattice<LAT>::Q, ST> p)
 {
     using L = Lattice<LAT>;
     const int x = blockIdx.x * kBlockX + threadIdx.x;
@@ -737,10 +784,10 @@ __global__ void __launch_bounds__(kBlockX) k_set_state(const Params<Lattice<LAT>
 // ---------------------------------------------------------------------------
 // Host-side dispatch for one lattice.
 
-template <int LAT, bool ROT, int MODE>
+template <int LAT, bool ROT, int MODE, typename ST>
 cudaError_t launch_mode(Op op, const Args &a, cudaStream_t s)
 {
-    const auto p = make_params<Lattice<LAT>::Q>(a);
+    const auto p = make_params<Lattice<LAT>::Q, ST>(a);
     const dim3 block(kBlockX);
     const dim3 grid((a.X + kBlockX - 1) / kBlockX, a.Y, a.Z);
     switch (op) {
@@ -754,13 +801,23 @@ cudaError_t launch_mode(Op op, const Args &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int LAT>
-cudaError_t launch_lattice(Op op, const Args &a, cudaStream_t s)
+template <int LAT, typename ST>
+cudaError_t launch_storage(Op op, const Args &a, cudaStream_t s)
 {
     const bool rot = a.Qr > 0;
     if (a.mode == 0)
-        return rot ? launch_mode<LAT, true, 0>(op, a, s) : launch_mode<LAT, false, 0>(op, a, s);
-    return rot ? launch_mode<LAT, true, 1>(op, a, s) : launch_mode<LAT, false, 1>(op, a, s);
+        return rot ? launch_mode<LAT, true, 0, ST>(op, a, s) : launch_mode<LAT, false, 0, ST>(op, a, s);
+    return rot ? launch_mode<LAT, true, 1, ST>(op, a, s) : launch_mode<LAT, false, 1, ST>(op, a, s);
+}
+
+template <int LAT>
+cudaError_t launch_lattice(Op op, const Args &a, cudaStream_t s)
+{
+    switch (a.storage) {
+    case 1: return launch_storage<LAT, __half>(op, a, s);
+    case 2: return launch_storage<LAT, __nv_bfloat16>(op, a, s);
+    default: return launch_storage<LAT, float>(op, a, s);
+    }
 }
 
 }  // namespace lbm

@@ -21,6 +21,7 @@ LATTICE_DIM = {"D1Q7": 1, "D2Q37": 2, "D2Q49": 2, "D3Q343": 3}
 LATTICE_Q = {"D1Q7": 7, "D2Q37": 37, "D2Q49": 49, "D3Q343": 343}
 BCS = {"periodic": 0, "copy": 1}
 MODES = {"stream": 0, "fd": 1}
+STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
 STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ESIZE", -3: "LBM_ECUDA",
           -4: "LBM_ENONFINITE", -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}
 
@@ -31,6 +32,7 @@ SIGNATURES = {
     "lbm_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                   ctypes.POINTER(_vp)]),
     "lbm_set_mode": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "lbm_set_storage": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_set_grid": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_size_t),
                                     ctypes.POINTER(ctypes.c_size_t)]),
@@ -118,7 +120,7 @@ class Lbm:
     """
 
     def __init__(self, lattice: str, n: int, tau: float, shape, bc, mode: str = "stream",
-                 m_fd: int = 10, device=None, stream=None):
+                 m_fd: int = 10, device=None, stream=None, storage: str = "f32"):
         import torch
 
         self.torch = torch
@@ -143,6 +145,8 @@ class Lbm:
                                             ctypes.byref(h)), None)
             self.h = h
             self._check(self.lib.lbm_set_mode(h, MODES[mode], int(m_fd)))
+            self._check(self.lib.lbm_set_storage(h, STORAGES[storage]))
+            self.storage = storage
             shp = (ctypes.c_int64 * 3)(*self.shape, *([1] * (3 - self.D)))
             bcs = (ctypes.c_int * 3)(*[BCS[b] for b in bc], *([0] * (3 - self.D)))
             sb = ctypes.c_size_t()
