@@ -201,6 +201,15 @@ int lattice_constants(int lattice, double *r, int e[][3], double *w)
         }
         return 49;
     }
+    if (lattice == LBM_D3Q343) {
+        *r = r1;
+        for (int i = 0; i < 343; ++i) {
+            const int ex = i % 7 - 3, ey = (i / 7) % 7 - 3, ez = i / 49 - 3;
+            e[i][0] = ex; e[i][1] = ey; e[i][2] = ez;
+            w[i] = v[std::abs(ex)] * v[std::abs(ey)] * v[std::abs(ez)];
+        }
+        return 343;
+    }
     if (lattice == LBM_D2Q37) {
         double W[8];
         *r = bisect_r([&](double x) { return d2q37_for_r(x, W); });
@@ -276,6 +285,7 @@ cudaError_t launch(lbm_ctx *h, Op op, const Args &a)
     case LBM_D1Q7: return lbm::launch_d1q7(op, a, h->stream);
     case LBM_D2Q37: return lbm::launch_d2q37(op, a, h->stream);
     case LBM_D2Q49: return lbm::launch_d2q49(op, a, h->stream);
+    case LBM_D3Q343: return lbm::launch_d3q343(op, a, h->stream);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -338,7 +348,6 @@ int lbm_create(int D, int lattice, int n, double tau, lbm_handle *out)
     *out = nullptr;
     if (D < 1 || D > 3) return LBM_EINVAL;
     if (lattice_dim(lattice) != D) return LBM_EINVAL;
-    if (lattice == LBM_D3Q343) return LBM_EINVAL;  // not built in this version
     if (n < 0 || !(tau > 0.0) || !std::isfinite(tau)) return LBM_EINVAL;
     lbm_ctx *h = new lbm_ctx();
     h->D = D;
@@ -377,6 +386,8 @@ int lbm_set_mode(lbm_handle h, int mode, int m_fd)
     if (h->grid_set) return fail(h, LBM_ESTATE, "lbm_set_mode must precede lbm_set_grid");
     if (mode != LBM_MODE_STREAM && mode != LBM_MODE_FD) return fail(h, LBM_EINVAL, "unknown mode");
     if (mode == LBM_MODE_FD && m_fd < 1) return fail(h, LBM_EINVAL, "m_fd must be >= 1");
+    if (mode == LBM_MODE_FD && h->lattice == LBM_D3Q343)
+        return fail(h, LBM_EINVAL, "D3Q343 has STREAM transport only");
     h->mode = mode;
     h->m_fd = (mode == LBM_MODE_FD) ? m_fd : 1;
     return LBM_OK;
@@ -403,7 +414,9 @@ int lbm_set_grid(lbm_handle h, const int64_t *shape, const int *bc, size_t *stat
     const int64_t pitch = (s[0] + row_align - 1) / row_align * row_align;
     const int64_t S = pitch * s[1] * s[2];
     // the kernels index the whole state buffer with 32-bit element offsets
-    if (S * (h->Q + h->Qr) > 0x7fffffffLL)
+    // the kernels index up to 49 populations with 32-bit element offsets
+    // (D3Q343 uses 64-bit ones); every per-population offset is 32-bit
+    if (S > 0x7fffffffLL || (h->Q <= 49 && S * (h->Q + h->Qr) > 0x7fffffffLL))
         return fail(h, LBM_ESIZE, "state buffer would exceed 2^31 floats");
     for (int a = 0; a < 3; ++a) {
         h->shape[a] = s[a];
@@ -672,6 +685,7 @@ extern "C" int lbm_conservation_noalloc(lbm_handle h, const void *state, void *s
     case LBM_D1Q7: e = lbm::launch_d1q7(Op::Conserve, a, s); break;
     case LBM_D2Q37: e = lbm::launch_d2q37(Op::Conserve, a, s); break;
     case LBM_D2Q49: e = lbm::launch_d2q49(Op::Conserve, a, s); break;
+    case LBM_D3Q343: e = lbm::launch_d3q343(Op::Conserve, a, s); break;
     default: e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "conservation kernel");

@@ -1,0 +1,161 @@
+// Kernel instantiations for the D3Q343 lattice (D1Q7 x D1Q7 x D1Q7) and its
+// two-pass STREAM step.
+//
+// 343 populations do not fit in registers, so the step reads its pulled
+// populations twice: a first pass accumulates rho, j and sum |e|^2 g (row
+// sums by (e_y, e_z), column sums by e_x), a second pass re-reads each value
+// (from L1/L2: a 128-node block touches 343 x 128 x 4 B = 175 KB between the
+// two reads) and writes its post-collision value.  The rest and the six unit
+// velocities are stored last with the float32 moment corrections, as in the
+// one- and two-dimensional kernels.  Element indices are 64-bit (the state
+// of a 384^3 grid holds 2 x 10^10 values).
+#include "lbm_step.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kQ343 = 343;
+
+template <bool ROT, typename ST>
+__global__ void __launch_bounds__(kBlockX) k_step_q343(const Params<kQ343, ST> p)
+{
+    constexpr int D = 3;
+    constexpr int C = (kQ343 - 1) / 2;  // rest velocity (171)
+    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.X) return;
+    const Offsets o = node_offsets<D>(p, x, y, z);
+    const int plane = p.pitch * p.Y;
+
+    // pass 1: moments of the pulled populations g_i(x) = ft_i(x - e_i)
+    float cs[7];
+#pragma unroll
+    for (int a = 0; a < 7; ++a) cs[a] = 0.f;
+    float rho = 0.f, jy = 0.f, jz = 0.f, e2yz = 0.f;
+    // e_y is unrolled so that each e_z plane issues its 49 loads at once
+    for (int c = 0; c < 7; ++c) {
+        const int zo = bc_wrap(z - (c - 3), p.Z, p.bc2) * plane;
+#pragma unroll
+        for (int b = 0; b < 7; ++b) {
+            const int row = zo + o.y[6 - b];
+            float rsum = 0.f;
+#pragma unroll
+            for (int a = 0; a < 7; ++a) {
+                const float g = ld(p, (c * 7 + b) * 7 + a, row + o.x[6 - a]);
+                cs[a] += g;
+                rsum += g;
+            }
+            const float db = (float)(b - 3), dc = (float)(c - 3);
+            rho += rsum;
+            jy = fmaf(db, rsum, jy);
+            jz = fmaf(dc, rsum, jz);
+            e2yz = fmaf(db * db + dc * dc, rsum, e2yz);
+        }
+    }
+    float jx = 0.f, e2 = e2yz;
+#pragma unroll
+    for (int k = 1; k <= 3; ++k) {
+        jx = fmaf((float)k, cs[3 + k] - cs[3 - k], jx);
+        e2 = fmaf((float)(k * k), cs[3 + k] + cs[3 - k], e2);
+    }
+    float h[7], R2 = 0.f;
+    if (ROT) {
+#pragma unroll
+        for (int j = 0; j < 7; ++j) h[j] = ld(p, kQ343 + j, o.self());
+#pragma unroll
+        for (int k = 1; k <= 3; ++k) R2 = fmaf((float)(k * k), h[3 + k] + h[3 - k], R2);
+    }
+    const Moments m = make_moments<D, ROT>(p, rho, jx, jy, jz, e2, R2);
+    if (!(m.rho > 0.f) || !(m.T > 0.f) || !(fabsf(m.T) < 3.0e38f)) atomicOr(p.status, 1);
+
+    // pass 2: equilibrium, BGK, store (rest and unit velocities deferred)
+    const float u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    const float om_rho = p.omega * m.rho;
+    const EqCoef k = eq_coef<D>(m.T, u2, om_rho);  // omega rho g^eq / w_i
+    const float keep = 1.0f - p.omega;
+    const float rux = m.ux * p.r, ruy = m.uy * p.r, ruz = m.uz * p.r;
+    const int self = o.self();
+    float acc0 = 0.f, acc2 = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+    float q_c = 0.f, q_mx = 0.f, q_px = 0.f, q_my = 0.f, q_py = 0.f, q_mz = 0.f, q_pz = 0.f;
+    float g_c = 0.f, g_mx = 0.f, g_px = 0.f, g_my = 0.f, g_py = 0.f, g_mz = 0.f, g_pz = 0.f;
+    // The correction sums are accumulated per row of 7 and then per plane, so
+    // each carries the rounding of ~2 x 7 additions rather than of 343.
+    for (int c = 0; c < 7; ++c) {
+        const int zo = bc_wrap(z - (c - 3), p.Z, p.bc2) * plane;
+        const int ez = c - 3;
+        float p0 = 0.f, p2 = 0.f, px = 0.f, py = 0.f;  // plane sums
+#pragma unroll
+        for (int b = 0; b < 7; ++b) {
+            const int row = zo + o.y[6 - b];
+            const int ey = b - 3;
+            const float cyz = fmaf((float)ey, ruy, (float)ez * ruz);
+            const int e2yz_i = ey * ey + ez * ez;
+            float r0 = 0.f, r2 = 0.f, rx = 0.f;  // row sums
+#pragma unroll
+            for (int a = 0; a < 7; ++a) {
+                const int ex = a - 3;
+                const int i = (c * 7 + b) * 7 + a;
+                const int E2 = ex * ex + e2yz_i;
+                const float cdot = fmaf((float)ex, rux, cyz);
+                const float q = p.w[i] * eq_single(k, cdot, p.r2 * (float)E2);
+                r0 += q;
+                r2 = fmaf((float)E2, q, r2);
+                if (ex) rx = fmaf((float)ex, q, rx);
+                const float g = ld(p, i, row + o.x[6 - a]);
+                if (E2 <= 1) {  // the rest and the six unit velocities: stored last
+                    if (E2 == 0) { q_c = q; g_c = g; }
+                    else if (ex == -1) { q_mx = q; g_mx = g; }
+                    else if (ex == 1) { q_px = q; g_px = g; }
+                    else if (ey == -1) { q_my = q; g_my = g; }
+                    else if (ey == 1) { q_py = q; g_py = g; }
+                    else if (ez == -1) { q_mz = q; g_mz = g; }
+                    else { q_pz = q; g_pz = g; }
+                } else {
+                    st(p, i, self, fmaf(keep, g, q));
+                }
+            }
+            p0 += r0;
+            p2 += r2;
+            px += rx;
+            py = fmaf((float)ey, r0, py);
+        }
+        acc0 += p0;
+        acc2 += p2;
+        ax += px;
+        ay += py;
+        az = fmaf((float)ez, p0, az);
+    }
+    const float d0 = om_rho - acc0;
+    const float d2 = p.omega * m.E2_eq - acc2;
+    const float bb = d2 * (0.5f / (float)D);
+    const float dmx = 0.5f * (p.omega * m.j[0] - ax);
+    const float dmy = 0.5f * (p.omega * m.j[1] - ay);
+    const float dmz = 0.5f * (p.omega * m.j[2] - az);
+    st(p, C, self, fmaf(keep, g_c, q_c + (d0 - d2)));
+    st(p, C - 1, self, fmaf(keep, g_mx, q_mx + (bb - dmx)));
+    st(p, C + 1, self, fmaf(keep, g_px, q_px + (bb + dmx)));
+    st(p, C - 7, self, fmaf(keep, g_my, q_my + (bb - dmy)));
+    st(p, C + 7, self, fmaf(keep, g_py, q_py + (bb + dmy)));
+    st(p, C - 49, self, fmaf(keep, g_mz, q_mz + (bb - dmz)));
+    st(p, C + 49, self, fmaf(keep, g_pz, q_pz + (bb + dmz)));
+
+    if (ROT) {
+        float adv[7];
+        rot_advect<D>(p, o, h, m, adv);
+        rot_store(p, self, h, m, adv);
+    }
+}
+
+}  // namespace
+
+template <bool ROT, typename ST> cudaError_t launch_step_q343(const Args &a, cudaStream_t s)
+{
+    const auto p = make_params<kQ343, ST>(a);
+    const dim3 grid((a.X + kBlockX - 1) / kBlockX, a.Y, a.Z);
+    k_step_q343<ROT, ST><<<grid, kBlockX, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_d3q343(Op op, const Args &a, cudaStream_t s) { return launch_lattice<4>(op, a, s); }
+
+}  // namespace lbm

@@ -6,7 +6,7 @@
 
 namespace lbm {
 
-constexpr int kMaxQ = 49;        // largest translational set built here (D2Q49)
+constexpr int kMaxQ = 343;       // largest translational set built here (D3Q343)
 constexpr int kRedThreads = 256; // threads per block of the conservation reduction
 constexpr int kRedSlots = 8;     // doubles per reduction partial
 constexpr int kMaxRedBlocks = 1024;
@@ -42,5 +42,6 @@ struct Args {
 cudaError_t launch_d1q7(Op op, const Args &a, cudaStream_t s);
 cudaError_t launch_d2q37(Op op, const Args &a, cudaStream_t s);
 cudaError_t launch_d2q49(Op op, const Args &a, cudaStream_t s);
+cudaError_t launch_d3q343(Op op, const Args &a, cudaStream_t s);
 
 }  // namespace lbm

@@ -86,6 +86,13 @@ __host__ __device__ constexpr D2Q37Table make_d2q37()
             }
     return t;
 }
+template <> struct Lattice<4> {  // D3Q343 = D1Q7 x D1Q7 x D1Q7
+    static constexpr int D = 3, Q = 343;
+    __host__ __device__ static constexpr int ex(int i) { return i % 7 - 3; }
+    __host__ __device__ static constexpr int ey(int i) { return (i / 7) % 7 - 3; }
+    __host__ __device__ static constexpr int ez(int i) { return i / 49 - 3; }
+};
+
 template <> struct Lattice<2> {
     static constexpr int D = 2, Q = 37;
     __host__ __device__ static constexpr int ex(int i) { return make_d2q37().x[i]; }
@@ -223,7 +230,9 @@ __device__ __forceinline__ Offsets node_offsets(const Params<Q, ST> &p, int x, i
 template <bool CG = false, int Q, typename ST>
 __device__ __forceinline__ float ld(const Params<Q, ST> &p, int pop, int off)
 {
-    const ST *a = p.src + ((uint32_t)pop * (uint32_t)p.S + (uint32_t)off);
+    // 32-bit element index up to 49 populations; D3Q343 states exceed 2^32
+    using Idx = typename std::conditional<(Q > 49), uint64_t, uint32_t>::type;
+    const ST *a = p.src + ((Idx)pop * (Idx)p.S + (Idx)(uint32_t)off);
     ST v;
     if constexpr (CG) v = __ldcg(a);
     else v = __ldg(a);
@@ -233,7 +242,8 @@ __device__ __forceinline__ float ld(const Params<Q, ST> &p, int pop, int off)
 template <int Q, typename ST>
 __device__ __forceinline__ void st(const Params<Q, ST> &p, int pop, int off, float v)
 {
-    ST *a = p.dst + ((uint32_t)pop * (uint32_t)p.S + (uint32_t)off);
+    using Idx = typename std::conditional<(Q > 49), uint64_t, uint32_t>::type;
+    ST *a = p.dst + ((Idx)pop * (Idx)p.S + (Idx)(uint32_t)off);
     if constexpr (std::is_same<ST, float>::value) *a = v;
     else *a = Storage<ST>::encode(v, pop < Q ? p.iw[pop] : p.iwr[pop - Q]);
 }
@@ -249,6 +259,10 @@ struct Moments {
     // j_a = sum_i e_ia g_i, T_lat = T / r^2, E2_eq = sum_i |e_i|^2 g_i^eq
     float j[3], T_lat, E2_eq;
 };
+
+template <int D_, bool ROT, int Q, typename ST>
+__device__ __forceinline__ Moments make_moments(const Params<Q, ST> &p, float rho, float jx,
+                                                float jy, float jz, float e2, float R2);
 
 template <int LAT, bool ROT, int Q, typename ST>
 __device__ __forceinline__ Moments node_moments(const Params<Q, ST> &p, const float *g,
@@ -291,6 +305,16 @@ __device__ __forceinline__ Moments node_moments(const Params<Q, ST> &p, const fl
 #pragma unroll
         for (int k = 1; k <= 3; ++k) R2 = fmaf((float)(k * k), h[3 + k] + h[3 - k], R2);
     }
+    return make_moments<L::D, ROT>(p, rho, jx, jy, jz, e2, R2);
+}
+
+// rho, u, T (Eq. T) from the lattice sums rho = sum g, j = sum e g,
+// e2 = sum |e|^2 g and R2 = sum_j (j-3)^2 h_j.
+template <int D_, bool ROT, int Q, typename ST>
+__device__ __forceinline__ Moments make_moments(const Params<Q, ST> &p, float rho, float jx,
+                                                float jy, float jz, float e2, float R2)
+{
+    constexpr int D = D_;
     Moments m;
     const float inv_rho = 1.0f / rho;
     m.rho = rho;
@@ -298,8 +322,8 @@ __device__ __forceinline__ Moments node_moments(const Params<Q, ST> &p, const fl
     m.j[1] = jy;
     m.j[2] = jz;
     m.ux = p.r * jx * inv_rho;
-    m.uy = (L::D >= 2) ? p.r * jy * inv_rho : 0.f;
-    m.uz = (L::D >= 3) ? p.r * jz * inv_rho : 0.f;
+    m.uy = (D >= 2) ? p.r * jy * inv_rho : 0.f;
+    m.uz = (D >= 3) ? p.r * jz * inv_rho : 0.f;
     m.K = 0.5f * p.r2 * e2;              // sum_i g_i xi_i^2 / 2
     m.R = ROT ? p.half_n_r2 * R2 : 0.f;  // sum_j (n/2) h_j eta_j^2
     // Eq. T evaluated in lattice units, then scaled once by r^2.  The factor
@@ -318,7 +342,7 @@ __device__ __forceinline__ Moments node_moments(const Params<Q, ST> &p, const fl
         m.T_lat = __fdiv_rn(0.5f * (e2 - jj) * inv_rho + (ROT ? p.half_n * R2 : 0.f), p.cT);
     }
     m.T = p.r2 * m.T_lat;
-    m.E2_eq = jj + (float)L::D * rho * m.T_lat;  // rho (u^2 + D T) / r^2
+    m.E2_eq = jj + (float)D * rho * m.T_lat;  // rho (u^2 + D T) / r^2
     return m;
 }
 
@@ -784,6 +808,9 @@ __global__ void __launch_bounds__(kBlockX) k_set_state(const Params<Lattice<LAT>
 // ---------------------------------------------------------------------------
 // Host-side dispatch for one lattice.
 
+// The D3Q343 step (lbm_d3q343.cu): STREAM transport only.
+template <bool ROT, typename ST> cudaError_t launch_step_q343(const Args &a, cudaStream_t s);
+
 template <int LAT, bool ROT, int MODE, typename ST>
 cudaError_t launch_mode(Op op, const Args &a, cudaStream_t s)
 {
@@ -791,7 +818,13 @@ cudaError_t launch_mode(Op op, const Args &a, cudaStream_t s)
     const dim3 block(kBlockX);
     const dim3 grid((a.X + kBlockX - 1) / kBlockX, a.Y, a.Z);
     switch (op) {
-    case Op::Step: k_step<LAT, ROT, MODE><<<grid, block, 0, s>>>(p); break;
+    case Op::Step:
+        if constexpr (LAT == 4) {  // 343 populations: the two-pass kernel
+            return launch_step_q343<ROT, ST>(a, s);
+        } else {
+            k_step<LAT, ROT, MODE><<<grid, block, 0, s>>>(p);
+        }
+        break;
     case Op::Init: k_init<LAT, ROT, MODE><<<grid, block, 0, s>>>(p); break;
     case Op::Moments: k_moments<LAT, ROT, MODE><<<grid, block, 0, s>>>(p); break;
     case Op::Conserve: k_conserve<LAT, ROT, MODE><<<a.red_blocks, kRedThreads, 0, s>>>(p); break;
@@ -805,9 +838,11 @@ template <int LAT, typename ST>
 cudaError_t launch_storage(Op op, const Args &a, cudaStream_t s)
 {
     const bool rot = a.Qr > 0;
-    if (a.mode == 0)
+    if (a.mode == 0 || LAT == 4)  // D3Q343 has no FD transport (the host rejects it)
         return rot ? launch_mode<LAT, true, 0, ST>(op, a, s) : launch_mode<LAT, false, 0, ST>(op, a, s);
-    return rot ? launch_mode<LAT, true, 1, ST>(op, a, s) : launch_mode<LAT, false, 1, ST>(op, a, s);
+    if constexpr (LAT != 4)
+        return rot ? launch_mode<LAT, true, 1, ST>(op, a, s) : launch_mode<LAT, false, 1, ST>(op, a, s);
+    return cudaErrorInvalidValue;
 }
 
 template <int LAT>
