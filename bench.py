@@ -150,7 +150,7 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
     b = LbmBatch(lengths, [w.n for w in wls], [w.tau for w in wls], mode="fd", m_fd=10,
                  device=dev, stream=stream)
     b.set_macro(rho, u, T)
-    threads = b.autotune(20)
+    threads, bps = b.autotune(20)
     b.set_macro(rho, u, T)
     b.run(3)                     # warm-up (graph build for a different step count)
     b.set_macro(rho, u, T)
@@ -173,7 +173,7 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
     pick = order[np.linspace(0, count - 1, sample).astype(int)]
     bs = LbmBatch(lengths[pick], [wls[k].n for k in pick], [wls[k].tau for k in pick],
                   mode="fd", m_fd=10, device=dev, stream=stream)
-    bs.set_block(threads)
+    bs.set_block(threads, bps)
     rs = np.concatenate([wls[k].rho for k in pick])
     us = np.concatenate([wls[k].u[0] for k in pick])
     Ts = np.concatenate([wls[k].T for k in pick])
@@ -204,12 +204,74 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
     plain_time = single_s * (count / sample) * steps
     return {"metric": "Mnode-updates/s (f+g), ensemble", "value": value,
             "unit": "Mnode-updates/s", "tubes": count, "nodes": total, "steps": steps,
-            "ms_total": dt * 1e3, "threads_per_block": threads, "launches": launches,
+            "ms_total": dt * 1e3, "threads_per_block": threads,
+            "blocks_per_sm": bps, "launches": launches,
             "stable_fraction": 1.0 - bad / count,
             "speedup_vs_per_tube_launches": plain_time / dt,
             "per_tube_baseline": f"{sample} length-stratified tubes x {sample_steps} lbm_step "
                                  f"launches each, scaled to {count} tubes x {steps} steps",
             "rel_l1_vs_per_tube": worst}
+
+
+def blast_leg(dev, L: int = 384, steps: int = 10, storage: str = "f16", oracle_L: int = 32,
+              oracle_steps: int = 50):
+    """The 3-D blast workload on D3Q343: L^3 nodes, rho = 1, a central sphere
+    of radius 32 L/384 at higher pressure, periodic, tau = 2/3, with the
+    populations stored as `storage` deviations.  Stable-envelope variant
+    (p = 1.5 inside, 0.5 outside: T in [0.5, 1.5]); the stated p = 1 / 0.1
+    puts T = 0.1 outside the 4th-order lattice's range and goes non-finite
+    within ~10 steps.  For n = 0 (gamma = 5/3) and n = 4 (gamma = 9/7, the
+    integer n nearest the stated gamma = 1.3).  Error against the FP64
+    oracle on the geometrically scaled oracle_L^3 problem after
+    oracle_steps steps."""
+    import torch
+
+    from oracle import oracle
+    from paper_1606_06107_gb300 import Lbm, workloads
+
+    hbm, _ = peaks()
+    out = {}
+    for n in (0, 4):
+        wl = workloads.blast_3d(L=L, radius=32 * L / 384, n=n, p_in=1.5, p_out=0.5)
+        g = Lbm("D3Q343", n, 2 / 3, (L, L, L), ("periodic",) * 3, device=dev, storage=storage)
+        g.set_macro(wl.rho, wl.u, wl.T)
+        del wl
+        g.step(2)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.step(steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        status = g.status()
+        state_gb = 2 * g.state_bytes / 1e9
+        del g
+        torch.cuda.empty_cache()
+        Q = 343 + (7 if n else 0)
+        gbs = L ** 3 * Q * 2 * 2 / (ms * 1e-3) / 1e9
+        # error against the FP64 oracle on the scaled problem
+        ws = workloads.blast_3d(L=oracle_L, radius=max(1.5, 32 * oracle_L / 384 * 2), n=n,
+                                p_in=1.5, p_out=0.5)
+        s = Lbm("D3Q343", n, 2 / 3, ws.shape, ws.bc, device=dev, storage=storage)
+        s.set_macro(ws.rho, ws.u, ws.T)
+        s.step(oracle_steps)
+        ref = oracle.Sim(oracle.D3Q343, n, 2 / 3, ws.shape, (0, 0, 0))
+        ref.set_macro(ws.rho, ws.u, ws.T)
+        ref.step(oracle_steps)
+        errs = [float(np.abs(x.cpu().numpy().astype(np.float64) - y).sum() / np.abs(y).sum())
+                for x, y in zip(s.moments(), ref.moments())]
+        out[f"n{n}"] = {"gamma": (3 + n + 2) / (3 + n), "ms_per_step": ms,
+                        "value": L ** 3 / ms / 1e3, "unit": "Mnode-updates/s",
+                        "algorithmic_GBps": gbs, "frac_of_hbm": gbs / hbm, "status": status,
+                        "state_GB_two_buffers": state_gb,
+                        "rel_l1_vs_fp64_oracle": {"rho": errs[0], "u": errs[1], "T": errs[2],
+                                                  "sample": f"{oracle_L}^3 scaled, "
+                                                            f"{oracle_steps} steps"}}
+    out["workload"] = (f"blast_3d {L}^3 D3Q343, {storage} deviation storage, stable-envelope "
+                       f"variant p 1.5 | 0.5")
+    return out
 
 
 def dist_setup(n_gpus):
@@ -263,6 +325,15 @@ def run_gpu(args):
     world, rank, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only != "all":  # one leg alone, at the given size (profiling runs)
+        if args.only == "batched":
+            res = batched_leg(dev, steps=args.batched_steps, count=args.batched_count,
+                              sample=min(48, args.batched_count))
+        else:
+            res = blast_leg(dev, L=args.blast_size, steps=args.blast_steps,
+                            oracle_L=min(16, args.blast_size), oracle_steps=5)
+        print(json.dumps(res), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
@@ -354,7 +425,10 @@ def run_gpu(args):
         return
     batched = None
     if world == 1 and not args.no_batched:
-        batched = batched_leg(dev)
+        batched = batched_leg(dev, steps=args.batched_steps, count=args.batched_count)
+    blast = None
+    if world == 1 and not args.no_blast:
+        blast = blast_leg(dev, L=args.blast_size, steps=args.blast_steps)
     cpu = None
     if world == 1 and not args.no_cpu:
         rate, steps, dt, threads = cpu_oracle_rate()
@@ -380,6 +454,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "batched": batched,
+        "blast_3d": blast,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -398,6 +473,13 @@ def main():
                          "stable-envelope variant")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the ensemble leg")
+    ap.add_argument("--no-blast", action="store_true", help="skip the 3-D D3Q343 leg")
+    ap.add_argument("--only", default="all", choices=["all", "batched", "blast"],
+                    help="run one leg alone (profiling)")
+    ap.add_argument("--batched-count", type=int, default=4096)
+    ap.add_argument("--batched-steps", type=int, default=4000)
+    ap.add_argument("--blast-size", type=int, default=384)
+    ap.add_argument("--blast-steps", type=int, default=10)
     ap.add_argument("--size", type=int, default=X, help="grid edge (profiling of smaller cases)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -243,13 +243,15 @@ int lbm_batch_get_moments(lbm_batch b, float *rho, float *u, float *T);
  * and the number of problems whose word is non-zero.  Synchronizing. */
 int lbm_batch_status(lbm_batch b, int *status, int *n_bad);
 
-/* Threads per block of the persistent launch: lbm_batch_set_block sets it
- * (32..1024, a multiple of 32); lbm_batch_autotune times `sample_steps`
- * steps of the bound ensemble for each of 128, 256, 512 and 1024 threads
- * with resident-block grids and keeps the fastest (returned in *threads).
- * Autotuning advances the state: call lbm_batch_set_macro afterwards. */
-int lbm_batch_set_block(lbm_batch b, int threads);
-int lbm_batch_autotune(lbm_batch b, int64_t sample_steps, int *threads);
+/* Shape of the persistent launch: threads per block (32..1024, a multiple of
+ * 32) and resident blocks per SM (0 = as many as fit; fewer keep more of
+ * each problem's state in L2).  lbm_batch_autotune times `sample_steps`
+ * steps of the bound ensemble for every pair of 128/256/512/1024 threads and
+ * 1/2/4/max blocks per SM and keeps the fastest (returned through the
+ * pointers, which may be NULL).  Autotuning advances the state: call
+ * lbm_batch_set_macro afterwards. */
+int lbm_batch_set_block(lbm_batch b, int threads, int blocks_per_sm);
+int lbm_batch_autotune(lbm_batch b, int64_t sample_steps, int *threads, int *blocks_per_sm);
 
 int64_t lbm_batch_launch_count(lbm_batch b);
 const char *lbm_batch_last_error(lbm_batch b);

@@ -182,12 +182,13 @@ struct lbm_batch_ctx {
     cudaStream_t stream = nullptr;
     int cur = 0;
     int threads = 256;
+    int blocks_per_sm = 0;  // resident blocks per SM of the persistent grid (0 = max)
     int64_t launches = 0;
     std::string err;
     struct Cached {
         cudaGraphExec_t exec = nullptr;
         long long steps = -1;
-        int cur = -1, threads = -1;
+        int cur = -1, threads = -1, bps = -1;
     } graphs[2];
     int next_graph = 0;
 };
@@ -233,7 +234,7 @@ BatchParams batch_params(const lbm_batch_ctx *b, long long steps)
 bool aligned(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
 
 // Resident-block grid of the persistent kernel for `threads` per block.
-cudaError_t persistent_grid(int mode, int threads, int *grid)
+cudaError_t persistent_grid(int mode, int threads, int bps, int *grid)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -243,7 +244,9 @@ cudaError_t persistent_grid(int mode, int threads, int *grid)
             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::k_batch_run<1>, threads, 0)
             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::k_batch_run<0>, threads, 0);
     if (e != cudaSuccess) return e;
-    *grid = std::max(1, per_sm) * sms;
+    per_sm = std::max(1, per_sm);
+    if (bps > 0) per_sm = std::min(per_sm, bps);
+    *grid = per_sm * sms;
     return cudaSuccess;
 }
 
@@ -251,7 +254,7 @@ cudaError_t persistent_grid(int mode, int threads, int *grid)
 int build_graph(lbm_batch b, long long steps, cudaGraphExec_t *exec)
 {
     int grid = 0;
-    cudaError_t e = persistent_grid(b->mode, b->threads, &grid);
+    cudaError_t e = persistent_grid(b->mode, b->threads, b->blocks_per_sm, &grid);
     if (e != cudaSuccess) return bcuda(b, e, "occupancy query");
     cudaGraph_t g = nullptr;
     e = cudaGraphCreate(&g, 0);
@@ -411,7 +414,9 @@ int lbm_batch_run(lbm_batch b, int64_t k)
     if (k == 0) return LBM_OK;
     lbm_batch_ctx::Cached *hit = nullptr;
     for (auto &c : b->graphs)
-        if (c.exec && c.steps == k && c.cur == b->cur && c.threads == b->threads) hit = &c;
+        if (c.exec && c.steps == k && c.cur == b->cur && c.threads == b->threads &&
+            c.bps == b->blocks_per_sm)
+            hit = &c;
     if (!hit) {
         hit = &b->graphs[b->next_graph];
         b->next_graph ^= 1;
@@ -422,6 +427,7 @@ int lbm_batch_run(lbm_batch b, int64_t k)
         hit->steps = k;
         hit->cur = b->cur;
         hit->threads = b->threads;
+        hit->bps = b->blocks_per_sm;
     }
     cudaError_t e = cudaGraphLaunch(hit->exec, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "cudaGraphLaunch");
@@ -463,48 +469,60 @@ int lbm_batch_status(lbm_batch b, int *status, int *n_bad)
     return LBM_OK;
 }
 
-int lbm_batch_set_block(lbm_batch b, int threads)
+int lbm_batch_set_block(lbm_batch b, int threads, int blocks_per_sm)
 {
     if (!b) return LBM_EINVAL;
     if (threads < 32 || threads > 1024 || threads % 32)
         return bfail(b, LBM_EINVAL, "threads must be a multiple of 32 in 32..1024");
+    if (blocks_per_sm < 0) return bfail(b, LBM_EINVAL, "blocks_per_sm must be >= 0");
     b->threads = threads;
+    b->blocks_per_sm = blocks_per_sm;
     return LBM_OK;
 }
 
-int lbm_batch_autotune(lbm_batch b, int64_t sample_steps, int *threads)
+int lbm_batch_autotune(lbm_batch b, int64_t sample_steps, int *threads, int *blocks_per_sm)
 {
     if (!b) return LBM_EINVAL;
     if (sample_steps < 1) return bfail(b, LBM_EINVAL, "sample_steps must be >= 1");
     if (!b->has_state) return bfail(b, LBM_ESTATE, "no state: call lbm_batch_set_macro");
-    static const int candidates[] = {128, 256, 512, 1024};
+    // Block size x resident blocks per SM: fewer resident problems keep more
+    // of each one's state in L2, more blocks hide more latency.
+    static const int cand_threads[] = {128, 256, 512, 1024};
+    static const int cand_bps[] = {1, 2, 4, 0};
     cudaEvent_t t0, t1;
     cudaError_t e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     if (e != cudaSuccess) return bcuda(b, e, "cudaEventCreate");
     float best_ms = 0.f;
-    int best = b->threads;
-    for (int c : candidates) {
-        b->threads = c;
-        int rc = lbm_batch_run(b, sample_steps);  // builds the graph, warms up
-        if (rc != LBM_OK) break;
-        e = cudaEventRecord(t0, b->stream);
-        rc = lbm_batch_run(b, sample_steps);
-        if (rc != LBM_OK) break;
-        if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-        if (e != cudaSuccess) break;
-        if (best_ms == 0.f || ms < best_ms) {
-            best_ms = ms;
-            best = c;
+    int best_t = b->threads, best_b = b->blocks_per_sm;
+    for (int c : cand_threads) {
+        for (int bps : cand_bps) {
+            b->threads = c;
+            b->blocks_per_sm = bps;
+            int rc = lbm_batch_run(b, sample_steps);  // builds the graph, warms up
+            if (rc != LBM_OK) break;
+            e = cudaEventRecord(t0, b->stream);
+            rc = lbm_batch_run(b, sample_steps);
+            if (rc != LBM_OK) break;
+            if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e != cudaSuccess) break;
+            if (best_ms == 0.f || ms < best_ms) {
+                best_ms = ms;
+                best_t = c;
+                best_b = bps;
+            }
         }
+        if (e != cudaSuccess) break;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
-    b->threads = best;
-    if (threads) *threads = best;
+    b->threads = best_t;
+    b->blocks_per_sm = best_b;
+    if (threads) *threads = best_t;
+    if (blocks_per_sm) *blocks_per_sm = best_b;
     if (e != cudaSuccess) return bcuda(b, e, "autotune timing");
     return LBM_OK;
 }

@@ -65,8 +65,9 @@ SIGNATURES = {
     "lbm_batch_get_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lbm_batch_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
-    "lbm_batch_set_block": (ctypes.c_int, [_vp, ctypes.c_int]),
-    "lbm_batch_autotune": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_set_block": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_autotune": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_launch_count": (_i64, [_vp]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_batch_destroy": (None, [_vp]),
@@ -342,14 +343,16 @@ class LbmBatch:
             self._check(self.lib.lbm_batch_status(self.h, st, ctypes.byref(bad)))
         return np.array(st[:]), bad.value
 
-    def set_block(self, threads: int):
-        self._check(self.lib.lbm_batch_set_block(self.h, int(threads)))
+    def set_block(self, threads: int, blocks_per_sm: int = 0):
+        self._check(self.lib.lbm_batch_set_block(self.h, int(threads), int(blocks_per_sm)))
 
-    def autotune(self, sample_steps: int = 20) -> int:
-        out = ctypes.c_int()
+    def autotune(self, sample_steps: int = 20):
+        """(threads per block, resident blocks per SM) of the fastest launch."""
+        t, b = ctypes.c_int(), ctypes.c_int()
         with self.torch.cuda.device(self.device):
-            self._check(self.lib.lbm_batch_autotune(self.h, int(sample_steps), ctypes.byref(out)))
-        return out.value
+            self._check(self.lib.lbm_batch_autotune(self.h, int(sample_steps), ctypes.byref(t),
+                                                    ctypes.byref(b)))
+        return t.value, b.value
 
     @property
     def launches(self) -> int:

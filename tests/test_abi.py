@@ -110,7 +110,8 @@ def test_batch_create_validation_and_sizes(lbmlib):
         assert tn.value == 83
         assert sb.value == 4 * 14 * (32 + 64 + 64)  # each problem padded to 32 floats
         assert lbmlib.lbm_batch_run(h, 1) == -6      # no state yet
-        assert lbmlib.lbm_batch_set_block(h, 100) == -1
-        assert lbmlib.lbm_batch_set_block(h, 512) == 0
+        assert lbmlib.lbm_batch_set_block(h, 100, 0) == -1
+        assert lbmlib.lbm_batch_set_block(h, 512, -1) == -1
+        assert lbmlib.lbm_batch_set_block(h, 512, 2) == 0
     finally:
         lbmlib.lbm_batch_destroy(h)

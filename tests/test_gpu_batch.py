@@ -96,8 +96,8 @@ def test_autotune_then_rerun_is_unchanged():
     b.set_macro(rho, u, T)
     b.run(10)
     first = [x.cpu().numpy() for x in b.moments()]
-    threads = b.autotune(5)
-    assert threads in (128, 256, 512, 1024)
+    threads, bps = b.autotune(5)
+    assert threads in (128, 256, 512, 1024) and bps in (0, 1, 2, 4)
     b.set_macro(rho, u, T)
     b.run(10)
     second = [x.cpu().numpy() for x in b.moments()]
