@@ -16,7 +16,10 @@ and its definition is the contract of the ``lbm_nn_*`` entry points in
     head      out      = x_N Wp^T + bp                            (3 channels)
     update    (rho,u,T)' = (rho,u,T) + out * out_scale
 
-with gelu the tanh form of the Gaussian error linear unit and bf16() rounding
+(patches of P consecutive nodes may form one position: 4P features in, 3P
+outputs; the functions below take the feature and output counts from the
+array shapes) with gelu the tanh form of the Gaussian error linear unit and
+bf16() rounding
 to bfloat16 (nearest, ties to even) at the points where the GPU path stores a
 bfloat16 tensor.  Training minimises the mean squared error between ``out``
 and the scaled change of the LBM state over K steps.  The backward pass is
@@ -167,7 +170,7 @@ def backward(p: Params, cache, gout, emulate_bf16=True):
     xs, zs, W, a = cache["xs"], cache["zs"], cache["W"], cache["a"]
     N = len(p.dil)
     k = p.W[0].shape[0] if N else 1
-    g2 = gout.reshape(-1, 3)
+    g2 = gout.reshape(-1, gout.shape[-1])
     gWp = g2.T @ xs[N].reshape(-1, xs[N].shape[-1])
     gbp = g2.sum(0)
     gx = gout @ p.Wp
@@ -177,7 +180,7 @@ def backward(p: Params, cache, gout, emulate_bf16=True):
         gW[i] = conv1d_weight_grad(gz, xs[i], k, p.dil[i])
         gb[i] = gz.reshape(-1, gz.shape[-1]).sum(0)
         gx = gx + conv1d_input_grad(gz, W[i], p.dil[i])
-    gWl = gx.reshape(-1, gx.shape[-1]).T @ a.reshape(-1, 4)
+    gWl = gx.reshape(-1, gx.shape[-1]).T @ a.reshape(-1, a.shape[-1])
     gbl = gx.reshape(-1, gx.shape[-1]).sum(0)
     return [gWl, gbl, *gW, *gb, gWp, gbp]
 

@@ -10,15 +10,17 @@ import pytest
 from oracle import surrogate_ref as S
 
 
-def small_params(C=6, k=5, dil=(1, 3, 2), seed=1):
+def small_params(C=6, k=5, dil=(1, 3, 2), seed=1, patch=1):
     p = S.init_params(C=C, k=k, dil=dil, seed=seed)
     rng = np.random.default_rng(seed + 10)
+    # patches of `patch` nodes: 4 patch features in, 3 patch outputs
+    p.Wl = rng.normal(0, 0.5, (C, 4 * patch))
     # nonzero biases and a larger body so that every term matters
     p.W = [w * 8 for w in p.W]
     p.b = [rng.normal(0, 0.3, C) for _ in dil]
     p.bl = rng.normal(0, 0.3, C)
-    p.bp = rng.normal(0, 0.3, 3)
-    p.Wp = rng.normal(0, 0.5, (3, C))
+    p.bp = rng.normal(0, 0.3, 3 * patch)
+    p.Wp = rng.normal(0, 0.5, (3 * patch, C))
     return p
 
 
@@ -27,13 +29,14 @@ def loss_of(p, a, target):
     return S.mse(out, target)[0]
 
 
-def test_gradient_matches_central_differences():
+@pytest.mark.parametrize("patch", [1, 2])
+def test_gradient_matches_central_differences(patch):
     """Every parameter block, exact arithmetic: analytic = (L(p+h) - L(p-h)) / 2h."""
     rng = np.random.default_rng(0)
-    p = small_params()
+    p = small_params(patch=patch)
     B, L = 2, 23          # ragged: the dilated taps reach past both ends
-    a = rng.normal(0, 1, (B, L, 4))
-    target = rng.normal(0, 1, (B, L, 3))
+    a = rng.normal(0, 1, (B, L, 4 * patch))
+    target = rng.normal(0, 1, (B, L, 3 * patch))
     out, cache = S.forward(p, a, emulate_bf16=False)
     _, gout = S.mse(out, target)
     grads = S.backward(p, cache, gout, emulate_bf16=False)
