@@ -257,6 +257,138 @@ int64_t lbm_batch_launch_count(lbm_batch b);
 const char *lbm_batch_last_error(lbm_batch b);
 void lbm_batch_destroy(lbm_batch b);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate: a 1-D convolutional operator that advances the
+ * macroscopic state (rho, u, T) of a tube by K lattice steps per call.  The
+ * paper has no counterpart: it is an extension of the method, which remains
+ * its fallback and its judge.  The network (all entry points below are its
+ * building blocks; the layer sequence is driven by the Python binding):
+ *   features  a[p]     = ((rho-1)/s0, u/s1, (T-1)/s2, (gamma-1.4)/s3)
+ *   lift      x0       = bf16(a Wl^T + bl)
+ *   layer i   z_i      = conv(x_i; W_i, d_i) + b_i,  W_i[t][co][ci], k taps,
+ *                        tap t reads position l + (t - k/2) d_i, zero outside
+ *                        the tube
+ *             x_{i+1}  = bf16(x_i + gelu(z_i)),  gelu in its tanh form
+ *   head      out      = x_N Wp^T + bp
+ *   update    (rho,u,T)' = (rho,u,T) + out * out_scale
+ * Patches of P consecutive nodes may be treated as one position (F = 4P
+ * features in, Fo = 3P outputs), which is a reinterpretation of the same
+ * channel-last buffers.
+ *
+ * Common conventions.  Every pointer is a device pointer unless stated;
+ * the caller owns every buffer; nothing is allocated.  Activations are
+ * channel-last [B][L][C] (tube b, position l, channel c) bfloat16 with C a
+ * multiple of 128, gradients of the residual stream float32 in the same
+ * layout, conv weights bfloat16 [k][C][C].  `impl` selects the tensor-core
+ * kernels (0: tcgen05 MMA fed by the Tensor Memory Accelerator, operands
+ * 16-byte aligned) or the CUDA-core ones (1).  `status` (device int, may be
+ * NULL) receives bit 4 if a tensor-core kernel gave up waiting on a
+ * barrier, in which case its outputs are not written.  Calls are
+ * asynchronous on `stream`; they return LBM_OK, LBM_EINVAL (bad pointer,
+ * shape, alignment or aliasing) or LBM_ECUDA (launch failure).
+ * ---------------------------------------------------------------------- */
+
+/* y = bf16(x + gelu(conv(x; w, dil) + bias)); z (may be NULL) receives
+ * bf16(conv(x) + bias).  x, y, z: [B][L][C]; w: [k][C][C] (W[t][co][ci]);
+ * bias: [C] float.  k odd, x != y. */
+int lbm_nn_conv_forward(const void *x, const void *w, const float *bias, void *y, void *z, int B,
+                        int L, int C, int k, int dil, int impl, int *status, void *stream);
+
+/* Input gradient of a conv layer, added to the residual-stream gradient:
+ * gx[b,l,ci] += sum_t sum_co gz[b, l - (t-k/2) dil, co] W[t][co][ci], given
+ * wt = the transposed, flipped weights WT[t][ci][co] = W[k-1-t][co][ci]
+ * (lbm_nn_cast_weights).  If zprev is not NULL, also the pre-activation
+ * gradient of the layer below: gzprev = bf16(gx_new * gelu'(zprev)). */
+int lbm_nn_conv_backward_data(const void *gz, const void *wt, float *gx, const void *zprev,
+                              void *gzprev, int B, int L, int C, int k, int dil, int impl,
+                              int *status, void *stream);
+
+/* Weight gradient, accumulated: gw[t][co][ci] += sum_{b,l} gz[b,l,co] *
+ * x[b, l + (t-k/2) dil, ci].  gw float [k][C][C], 16-byte aligned. */
+int lbm_nn_conv_backward_weight(const void *gz, const void *x, float *gw, int B, int L, int C, int k,
+                                int dil, int impl, int *status, void *stream);
+
+/* bf16 copies of `layers` float conv weights [layers][k][C][C]: w_bf16 in
+ * the same layout, wt_bf16 (may be NULL) transposed and flipped per layer. */
+int lbm_nn_cast_weights(const float *w, void *w_bf16, void *wt_bf16, int layers, int C, int k,
+                        void *stream);
+
+/* Lift: x0[p][c] = bf16(sum_j feat[p][j] Wl[c][j] + bl[c]) for P positions
+ * of F <= 64 float features; C <= 256. */
+int lbm_nn_lift(const float *feat, const float *Wl, const float *bl, void *x0, int64_t P, int F,
+                int C, void *stream);
+
+/* Lift backward, accumulated: gWl[c][j] += sum_p gx0[p][c] feat[p][j],
+ * gbl[c] += sum_p gx0[p][c].  C a multiple of 32, at most 1024. */
+int lbm_nn_lift_backward(const float *gx0, const float *feat, float *gWl, float *gbl, int64_t P,
+                         int F, int C, void *stream);
+
+/* Head: out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o], Fo <= 16 float outputs. */
+int lbm_nn_head(const void *x, const float *Wp, const float *bp, float *out, int64_t P, int C, int Fo,
+                void *stream);
+
+/* Head backward: gx = gout Wp (written), gz = bf16(gx * gelu'(z)) (written;
+ * z is the pre-activation of the last conv layer), gWp += gout^T x,
+ * gbp += sum_p gout.  C a multiple of 32, at most 256. */
+int lbm_nn_head_backward(const float *gout, const void *x, const float *Wp, const void *z, float *gx,
+                         void *gz, float *gWp, float *gbp, int64_t P, int C, int Fo, void *stream);
+
+/* Bias gradient of a conv layer, accumulated: gb[c] += sum_p gz[p][c]. */
+int lbm_nn_bias_grad(const void *gz, float *gb, int64_t P, int C, void *stream);
+
+/* One Adam step (Kingma and Ba, bias-corrected, step number t >= 1) on n
+ * float parameters: g += weight_decay p; m, v moment estimates updated in
+ * place; p -= lr m_hat / (sqrt(v_hat) + eps). */
+int lbm_nn_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                float eps, int t, float weight_decay, void *stream);
+
+/* Mean squared error: *loss += mean((out - target)^2) (device double, the
+ * caller zeroes it); gout (may be NULL) = 2 (out - target) / n. */
+int lbm_nn_mse(const float *out, const float *target, float *gout, double *loss, int64_t n,
+               void *stream);
+
+/* Features of B tubes of L nodes: feat[b*L+l] = the four values above;
+ * gamma[B] per tube; in_scale: 4 HOST floats.  feat 16-byte aligned. */
+int lbm_nn_features(const float *rho, const float *u, const float *T, const float *gamma, float *feat,
+                    int B, int L, const float *in_scale, void *stream);
+
+/* Training targets: target[i] = ((rho2-rho)/s0, (u2-u)/s1, (T2-T)/s2) for n
+ * nodes; out_scale: 3 HOST floats. */
+int lbm_nn_targets(const float *rho, const float *u, const float *T, const float *rho2,
+                   const float *u2, const float *T2, float *target, int64_t n,
+                   const float *out_scale, void *stream);
+
+/* Update: (rho2, u2, T2) = (rho, u, T) + out * out_scale (HOST floats). */
+int lbm_nn_apply(const float *rho, const float *u, const float *T, const float *out, float *rho2,
+                 float *u2, float *T2, int64_t n, const float *out_scale, void *stream);
+
+/* Per-tube checks over the window [w0, w0+W) of B tubes of L nodes between
+ * a state (rho, u, T) and a second state (rho2, u2, T2):
+ *   residual[b] (may be NULL) = max of the relative changes of the totals of
+ *     mass, momentum (relative to the mass) and energy
+ *     rho ((1+n)/2 T + u^2/2), half_dof[b] = (1+n)/2;
+ *   l1[b] (may be NULL) = max over rho, u, T of sum|first - second| over
+ *     the window divided by sum|rho2|, sum sqrt(gamma T2) and sum|T2|
+ *     (the second state is the reference). */
+int lbm_nn_tube_checks(const float *rho, const float *u, const float *T, const float *rho2,
+                       const float *u2, const float *T2, const float *half_dof, const float *gamma,
+                       float *residual, float *l1, int B, int L, int w0, int W, void *stream);
+
+/* Row gather of three float fields stored as rows of row_len nodes:
+ * d_f[i*W + w] = f[rows[i]*row_len + offsets[i] + w] for i < count, w < W
+ * (rows: device int64, offsets: device int or NULL for 0).  Used for the
+ * training minibatches, the spot-check windows and the fallback tubes; the
+ * caller keeps offsets[i] + W <= row_len. */
+int lbm_nn_gather(const float *a, const float *b, const float *c, const int64_t *rows,
+                  const int *offsets, int count, int64_t row_len, int W, float *da, float *db,
+                  float *dc, void *stream);
+
+/* The reverse assignment: f[rows[i]*row_len + offsets[i] + w] = d_f[i*W + w]
+ * (here a, b, c are the packed rows and da, db, dc the row-major fields). */
+int lbm_nn_scatter(const float *a, const float *b, const float *c, const int64_t *rows,
+                   const int *offsets, int count, int64_t row_len, int W, float *da, float *db,
+                   float *dc, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,1187 @@
+// Kernels of the learned surrogate: a 1-D convolutional operator over tubes
+// that advances the macroscopic state (rho, u, T) by K lattice steps per call
+// (the lbm_nn_* entry points of include/lbm.h).  The paper has no such
+// network; it is an extension whose fallback and judge is the lattice
+// Boltzmann method itself.
+//
+// Data layout (channel-last, one tube after another):
+//   activations x[b][l][c] bfloat16, C channels (C a multiple of 128);
+//   pre-activations z[b][l][c] bfloat16; residual-stream gradients gx fp32;
+//   weights W[t][co][ci] bfloat16 (k taps, tap t reads position l + (t-k/2)d,
+//   zero outside the tube), their transposed and flipped copy
+//   WT[t][ci][co] = W[k-1-t][co][ci] for the input gradient.
+//
+// The three convolution products are implicit GEMMs on the fifth-generation
+// tensor cores: the Tensor Memory Accelerator copies 128-byte-swizzled tiles
+// straight out of the channel-last tensors (the tap shift is a coordinate
+// offset; rows outside the tube come back as zeros), one thread issues
+// tcgen05.mma into a 128 x 128 fp32 accumulator in tensor memory, and four
+// warps drain it with tcgen05.ld into a fused epilogue.
+//   forward       D[pos][co] = sum_{t,ci} x[pos+s_t][ci] W[t][co][ci]   (A, B K-major)
+//   input grad    D[pos][ci] = sum_{t,co} gz[pos+s_t][co] WT[t][ci][co] (A, B K-major)
+//   weight grad   D[co][ci]  = sum_pos gz[pos][co] x[pos+s_t][ci]       (A, B MN-major)
+// A CUDA-core implementation of the same three products (impl = 1) is kept
+// as the comparison point for the tensor-core one.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/lbm.h"
+
+namespace {
+
+// ---------------------------------------------------------------- constants
+constexpr int kTile = 128;          // accumulator rows and columns
+constexpr int kChunk = 64;          // bf16 elements in one 128-byte swizzle row
+constexpr int kStages = 3;          // pipeline depth
+constexpr int kStageBytes = 32768;  // A tile + B tile (16 KB each)
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 128;  // + alignment + barriers
+constexpr int kWgRows = 64;         // positions per weight-gradient stage
+constexpr long long kWaitCycles = 1ll << 32;  // bound on every mbarrier wait (~2 s)
+constexpr int kTimeoutBit = 4;      // status bit set when a wait gives up
+
+// ------------------------------------------------------------ math helpers
+__device__ __forceinline__ float gelu(float x)
+{
+    const float c = 0.7978845608028654f;  // sqrt(2/pi)
+    const float th = tanhf(c * fmaf(0.044715f * x, x * x, x));
+    return 0.5f * x * (1.0f + th);
+}
+
+__device__ __forceinline__ float gelu_grad(float x)
+{
+    const float c = 0.7978845608028654f;
+    const float th = tanhf(c * fmaf(0.044715f * x, x * x, x));
+    return 0.5f * (1.0f + th) + 0.5f * x * (1.0f - th * th) * c * fmaf(3.0f * 0.044715f * x, x, 1.0f);
+}
+
+__device__ __forceinline__ void unpack8(const uint4 &q, float *v)
+{
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f = __bfloat1622float2(h[i]);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+
+__device__ __forceinline__ uint4 pack8(const float *v)
+{
+    uint4 q;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    return q;
+}
+
+// ------------------------------------------------- barriers, TMA, tcgen05
+__device__ __forceinline__ uint32_t saddr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(saddr(bar)), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// Wait for the phase of `bar` with the given parity to complete; gives up
+// after kWaitCycles, sets the timeout bit and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            if (status) atomicOr(status, kTimeoutBit);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(saddr(dst)), "l"(map), "r"(x), "r"(y), "r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y, int z)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(saddr(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(saddr(bar)) : "memory");
+}
+
+// Shared-memory matrix descriptor, 128-byte swizzle: start address, leading
+// and stride byte offsets (16-byte units), descriptor version 1, layout 2.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= 1ull << 46;
+    d |= 2ull << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B,
+// M = N = 128, operand majorness (0 = K-major, 1 = MN-major).
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t a_mn, uint32_t b_mn)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn << 15) | (b_mn << 16) |
+           ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 32 consecutive fp32 columns of the accumulator.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    // the wait takes the registers as operands so that no use moves above it
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                   "+r"(r[30]), "+r"(r[31])
+                 :: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------ GEMM kernels
+enum Epi : int { kEpiForward = 0, kEpiInputGrad = 1 };
+
+struct ConvArgs {
+    int B, L, C, k, dil;
+    const __nv_bfloat16 *x;    // forward: residual input (= the A tensor)
+    const float *bias;         // forward: [C]
+    __nv_bfloat16 *y;          // forward: output
+    __nv_bfloat16 *z;          // forward: pre-activation (may be null)
+    float *gx;                 // input grad: residual-stream gradient, updated in place
+    const __nv_bfloat16 *zprev;  // input grad: pre-activation of the layer below (may be null)
+    __nv_bfloat16 *gzprev;     // input grad: its gradient, bf16(gx * gelu'(zprev))
+    int *status;
+};
+
+struct Smem {
+    uint8_t *tiles;
+    uint64_t *full, *empty, *done;
+    uint32_t *tmem_slot;
+};
+
+__device__ __forceinline__ Smem carve(uint8_t *raw)
+{
+    Smem s;
+    s.tiles = (uint8_t *)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(s.tiles + kStages * kStageBytes);
+    s.full = bars;
+    s.empty = bars + kStages;
+    s.done = bars + 2 * kStages;
+    s.tmem_slot = (uint32_t *)(bars + 2 * kStages + 1);
+    return s;
+}
+
+__device__ __forceinline__ void setup(const Smem &s)
+{
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&s.full[i], 1);
+            mbar_init(&s.empty[i], 1);
+        }
+        mbar_init(s.done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(saddr(s.tmem_slot)), "r"(kTile) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__device__ __forceinline__ void teardown(uint32_t tmem)
+{
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile)
+                     : "memory");
+    }
+}
+
+// Producer side shared by the kernels: after a failed wait, wait (bounded)
+// for the loads already issued so that none lands after the block exits.
+__device__ __forceinline__ void drain(const Smem &s, int issued, int *status)
+{
+    for (int kb = std::max(0, issued - kStages); kb < issued; ++kb)
+        mbar_wait(&s.full[kb % kStages], (kb / kStages) & 1, status);
+}
+
+// Forward and input-gradient convolution: one 128-position x 128-channel
+// output tile per block, K = k taps x C channels in 64-channel steps.
+template <int EPI>
+__global__ void __launch_bounds__(128, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
+              ConvArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const Smem s = carve(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int l0 = blockIdx.x * kTile, n0 = blockIdx.y * kTile, b = blockIdx.z;
+    const int chunks = a.C / kChunk, nk = a.k * chunks;
+    setup(s);
+    const uint32_t tmem = *s.tmem_slot;
+    __shared__ volatile int failed;
+    if (threadIdx.x == 0) failed = 0;
+    __syncthreads();
+
+    if (warp == 0 && lane == 0) {  // TMA producer
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int st = kb % kStages, use = kb / kStages;
+            if (use > 0 && !mbar_wait(&s.empty[st], (use - 1) & 1, a.status)) {
+                failed = 1;
+                break;
+            }
+            const int t = kb / chunks, c0 = (kb % chunks) * kChunk;
+            uint8_t *tile = s.tiles + st * kStageBytes;
+            mbar_expect_tx(&s.full[st], kStageBytes);
+            tma_load_3d(tile, &map_a, &s.full[st], c0, l0 + (t - a.k / 2) * a.dil, b);
+            tma_load_2d(tile + kStageBytes / 2, &map_w, &s.full[st], c0, t * a.C + n0);
+        }
+        if (kb < nk) drain(s, kb, a.status);
+    } else if (warp == 1 && lane == 0) {  // MMA issuer
+        constexpr uint32_t idesc = instr_desc(0, 0);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int st = kb % kStages;
+            if (!mbar_wait(&s.full[st], (kb / kStages) & 1, a.status)) {
+                failed = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t at = saddr(s.tiles + st * kStageBytes);
+            const uint32_t bt = at + kStageBytes / 2;
+#pragma unroll
+            for (int kk = 0; kk < kChunk / 16; ++kk)
+                mma_bf16(tmem, smem_desc(at + kk * 32, 16, 1024), smem_desc(bt + kk * 32, 16, 1024),
+                         idesc, (kb | kk) != 0);
+            mma_commit(&s.empty[st]);
+        }
+        mma_commit(s.done);
+    }
+    __syncwarp();
+    if (!mbar_wait(s.done, 0, a.status)) failed = 1;
+    __syncwarp();
+    tc_fence_after();
+
+    const int row = warp * 32 + lane, l = l0 + row;
+    const bool ok = l < a.L;
+    const int64_t base = ((int64_t)b * a.L + l) * a.C + n0;
+#pragma unroll 1
+    for (int c = 0; c < kTile; c += 32) {
+        float v[32];
+        __syncwarp();  // tcgen05.ld is warp-collective
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+        if (!ok || failed) continue;
+        if constexpr (EPI == kEpiForward) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float xr[8], yv[8], zv[8];
+                unpack8(*reinterpret_cast<const uint4 *>(a.x + base + c + 8 * q), xr);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float zz = v[8 * q + j] + __ldg(a.bias + n0 + c + 8 * q + j);
+                    zv[j] = zz;
+                    yv[j] = xr[j] + gelu(zz);
+                }
+                *reinterpret_cast<uint4 *>(a.y + base + c + 8 * q) = pack8(yv);
+                if (a.z) *reinterpret_cast<uint4 *>(a.z + base + c + 8 * q) = pack8(zv);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float g[8];
+                float4 *gp = reinterpret_cast<float4 *>(a.gx + base + c + 8 * q);
+                const float4 g0 = gp[0], g1 = gp[1];
+                g[0] = g0.x + v[8 * q + 0]; g[1] = g0.y + v[8 * q + 1];
+                g[2] = g0.z + v[8 * q + 2]; g[3] = g0.w + v[8 * q + 3];
+                g[4] = g1.x + v[8 * q + 4]; g[5] = g1.y + v[8 * q + 5];
+                g[6] = g1.z + v[8 * q + 6]; g[7] = g1.w + v[8 * q + 7];
+                gp[0] = make_float4(g[0], g[1], g[2], g[3]);
+                gp[1] = make_float4(g[4], g[5], g[6], g[7]);
+                if (a.gzprev) {
+                    float zp[8], gz[8];
+                    unpack8(*reinterpret_cast<const uint4 *>(a.zprev + base + c + 8 * q), zp);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) gz[j] = g[j] * gelu_grad(zp[j]);
+                    *reinterpret_cast<uint4 *>(a.gzprev + base + c + 8 * q) = pack8(gz);
+                }
+            }
+        }
+    }
+    teardown(tmem);
+}
+
+// Weight gradient: one block reduces the positions of blocks [q0, q1) (64
+// positions each, tubes one after another) for one tap and one 128 x 128
+// (co, ci) tile, then adds its tile to gw with coalesced vector reductions.
+__global__ void __launch_bounds__(128, 1)
+    k_wgrad_tc(const __grid_constant__ CUtensorMap map_g, const __grid_constant__ CUtensorMap map_x,
+               float *gw, int B, int L, int C, int k, int dil, int per_block, int *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const Smem s = carve(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = C / kTile;
+    const int t = blockIdx.y / (tiles * tiles);
+    const int co0 = ((blockIdx.y / tiles) % tiles) * kTile, ci0 = (blockIdx.y % tiles) * kTile;
+    const int nblk = (L + kWgRows - 1) / kWgRows;
+    const int total = B * nblk;
+    const int q0 = blockIdx.x * per_block, q1 = std::min(total, q0 + per_block);
+    if (q0 >= q1) return;  // uniform across the block, before any allocation
+    const int nk = q1 - q0, shift = (t - k / 2) * dil;
+    setup(s);
+    const uint32_t tmem = *s.tmem_slot;
+    __shared__ volatile int failed;
+    if (threadIdx.x == 0) failed = 0;
+    __syncthreads();
+
+    if (warp == 0 && lane == 0) {
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int st = kb % kStages, use = kb / kStages;
+            if (use > 0 && !mbar_wait(&s.empty[st], (use - 1) & 1, status)) {
+                failed = 1;
+                break;
+            }
+            const int q = q0 + kb, bb = q / nblk, lb = (q % nblk) * kWgRows;
+            uint8_t *tile = s.tiles + st * kStageBytes;
+            mbar_expect_tx(&s.full[st], kStageBytes);
+            // A = gz rows lb..lb+63, channel blocks co0 and co0+64 (8 KB each)
+            tma_load_3d(tile, &map_g, &s.full[st], co0, lb, bb);
+            tma_load_3d(tile + 8192, &map_g, &s.full[st], co0 + kChunk, lb, bb);
+            // B = x rows lb+shift.., channel blocks ci0 and ci0+64
+            tma_load_3d(tile + 16384, &map_x, &s.full[st], ci0, lb + shift, bb);
+            tma_load_3d(tile + 24576, &map_x, &s.full[st], ci0 + kChunk, lb + shift, bb);
+        }
+        if (kb < nk) drain(s, kb, status);
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = instr_desc(1, 1);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int st = kb % kStages;
+            if (!mbar_wait(&s.full[st], (kb / kStages) & 1, status)) {
+                failed = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t at = saddr(s.tiles + st * kStageBytes);
+            const uint32_t bt = at + kStageBytes / 2;
+            // 16 positions = two 8-row swizzle atoms (2048 bytes) per MMA;
+            // the two 64-channel blocks are 8192 bytes apart
+#pragma unroll
+            for (int kk = 0; kk < kWgRows / 16; ++kk)
+                mma_bf16(tmem, smem_desc(at + kk * 2048, 8192, 1024),
+                         smem_desc(bt + kk * 2048, 8192, 1024), idesc, (kb | kk) != 0);
+            mma_commit(&s.empty[st]);
+        }
+        mma_commit(s.done);
+    }
+    __syncwarp();
+    if (!mbar_wait(s.done, 0, status)) failed = 1;
+    __syncwarp();
+    tc_fence_after();
+
+    // stage 32 x 32 blocks through shared memory (the pipeline buffers are
+    // free once the last MMA has completed) so that a warp adds 32
+    // consecutive columns of one row at a time
+    float *stage = reinterpret_cast<float *>(s.tiles) + warp * 32 * 33;
+#pragma unroll 1
+    for (int c = 0; c < kTile; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];
+        __syncwarp();
+        if (!failed) {
+            // lane handles 4 consecutive columns of rows r = lane/8 + 4i
+            const int cc = (lane & 7) * 4;
+#pragma unroll 1
+            for (int r = lane >> 3; r < 32; r += 4) {
+                const int co = co0 + warp * 32 + r;
+                float *dst = gw + ((int64_t)t * C + co) * C + ci0 + c + cc;
+                const float *src = stage + r * 33 + cc;
+                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                             ::"l"(dst), "f"(src[0]), "f"(src[1]), "f"(src[2]), "f"(src[3])
+                             : "memory");
+            }
+        }
+        __syncwarp();
+    }
+    teardown(tmem);
+}
+
+// ------------------------------------------------- CUDA-core comparison path
+constexpr int kSimtTX = 128, kSimtTC = 64, kSimtCI = 32, kSimtMaxK = 7;
+constexpr int kSimtMaxSpan = kSimtTX + (kSimtMaxK - 1) * 16;
+
+// out tile [128 positions][64 channels] of sum_t in[pos + s_t][ci] w[t][n][ci]
+__device__ __forceinline__ void simt_tile(const __nv_bfloat16 *in, const __nv_bfloat16 *w, int L,
+                                          int C, int k, int dil, int b, int x0, int n0,
+                                          float (&acc)[8][4])
+{
+    __shared__ float xs[kSimtMaxSpan][kSimtCI + 1];
+    __shared__ float ws[kSimtTC][kSimtMaxK][kSimtCI + 1];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int half = k / 2, span = kSimtTX + (k - 1) * dil;
+    for (int ci0 = 0; ci0 < C; ci0 += kSimtCI) {
+        for (int e = tid; e < span * kSimtCI; e += 256) {
+            const int r = e / kSimtCI, c = e % kSimtCI, l = x0 - half * dil + r;
+            xs[r][c] = (l >= 0 && l < L) ? __bfloat162float(in[((int64_t)b * L + l) * C + ci0 + c]) : 0.f;
+        }
+        for (int e = tid; e < kSimtTC * k * kSimtCI; e += 256) {
+            const int c = e % kSimtCI, t = (e / kSimtCI) % k, o = e / (kSimtCI * k);
+            ws[o][t][c] = __bfloat162float(w[((int64_t)t * C + n0 + o) * C + ci0 + c]);
+        }
+        __syncthreads();
+        for (int t = 0; t < k; ++t) {
+#pragma unroll 4
+            for (int c = 0; c < kSimtCI; ++c) {
+                float wv[4], xv[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) wv[j] = ws[tx * 4 + j][t][c];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) xv[i] = xs[ty * 8 + i + t * dil][c];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xv[i], wv[j], acc[i][j]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(256) k_conv_simt(const __nv_bfloat16 *in, const __nv_bfloat16 *w,
+                                                   ConvArgs a)
+{
+    const int x0 = blockIdx.x * kSimtTX, n0 = blockIdx.y * kSimtTC, b = blockIdx.z;
+    float acc[8][4] = {};
+    simt_tile(in, w, a.L, a.C, a.k, a.dil, b, x0, n0, acc);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int l = x0 + ty * 8 + i;
+        if (l >= a.L) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx * 4 + j;
+            const int64_t o = ((int64_t)b * a.L + l) * a.C + n;
+            if constexpr (EPI == kEpiForward) {
+                const float zz = acc[i][j] + a.bias[n];
+                a.y[o] = __float2bfloat16_rn(__bfloat162float(a.x[o]) + gelu(zz));
+                if (a.z) a.z[o] = __float2bfloat16_rn(zz);
+            } else {
+                const float g = a.gx[o] + acc[i][j];
+                a.gx[o] = g;
+                if (a.gzprev) a.gzprev[o] = __float2bfloat16_rn(g * gelu_grad(__bfloat162float(a.zprev[o])));
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_wgrad_simt(const __nv_bfloat16 *gz, const __nv_bfloat16 *x,
+                                                    float *gw, int L, int C, int k, int dil)
+{
+    __shared__ float gs[kSimtTX][kSimtTC + 1];
+    __shared__ float xs[kSimtMaxSpan][kSimtCI + 1];
+    const int tid = threadIdx.x, x0 = blockIdx.x * kSimtTX, b = blockIdx.z;
+    const int ntc = C / kSimtTC;
+    const int co0 = (blockIdx.y % ntc) * kSimtTC, ci0 = (blockIdx.y / ntc) * kSimtCI;
+    const int half = k / 2, span = kSimtTX + (k - 1) * dil;
+    for (int e = tid; e < kSimtTX * kSimtTC; e += 256) {
+        const int r = e / kSimtTC, o = e % kSimtTC, l = x0 + r;
+        gs[r][o] = l < L ? __bfloat162float(gz[((int64_t)b * L + l) * C + co0 + o]) : 0.f;
+    }
+    for (int e = tid; e < span * kSimtCI; e += 256) {
+        const int r = e / kSimtCI, c = e % kSimtCI, l = x0 - half * dil + r;
+        xs[r][c] = (l >= 0 && l < L) ? __bfloat162float(x[((int64_t)b * L + l) * C + ci0 + c]) : 0.f;
+    }
+    __syncthreads();
+    for (int pair = tid; pair < kSimtTC * kSimtCI; pair += 256) {
+        const int o = pair / kSimtCI, c = pair % kSimtCI;
+        for (int t = 0; t < k; ++t) {
+            float sum = 0.f;
+            for (int r = 0; r < kSimtTX; ++r) sum = fmaf(gs[r][o], xs[r + t * dil][c], sum);
+            atomicAdd(&gw[((int64_t)t * C + co0 + o) * C + ci0 + c], sum);
+        }
+    }
+}
+
+// ------------------------------------------------------------ small kernels
+int grid_for(int64_t n, int threads = 256)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 16));
+}
+
+// x0[p][c] = bf16(sum_j feat[p][j] Wl[c][j] + bl[c]); F <= 64 features
+__global__ void k_lift(const float *feat, const float *Wl, const float *bl, __nv_bfloat16 *x0,
+                       int64_t P, int F, int C)
+{
+    extern __shared__ float wsh[];  // [C][F] then [C]
+    for (int i = threadIdx.x; i < C * F; i += blockDim.x) wsh[i] = Wl[i];
+    for (int i = threadIdx.x; i < C; i += blockDim.x) wsh[C * F + i] = bl[i];
+    __syncthreads();
+    const int64_t n = P * C;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i / C;
+        const int c = (int)(i % C);
+        float s = wsh[C * F + c];
+        for (int j = 0; j < F; ++j) s = fmaf(feat[p * F + j], wsh[c * F + j], s);
+        x0[i] = __float2bfloat16_rn(s);
+    }
+}
+
+// out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o]: one warp per position.
+__global__ void k_head(const __nv_bfloat16 *x, const float *Wp, const float *bp, float *out,
+                       int64_t P, int C, int Fo)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
+        for (int o = 0; o < Fo; ++o) {
+            float s = 0.f;
+            for (int c = lane; c < C; c += 32)
+                s = fmaf(__bfloat162float(x[p * C + c]), __ldg(Wp + o * C + c), s);
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) out[p * Fo + o] = s + bp[o];
+        }
+    }
+}
+
+// Head backward: gx = gout Wp; gz = bf16(gx gelu'(z)); gWp += gout^T x; gbp += sum gout.
+// One warp per position, lanes over channels (C <= 256, Fo <= 16).
+__global__ void k_head_bwd(const float *gout, const __nv_bfloat16 *x, const float *Wp,
+                           const __nv_bfloat16 *z, float *gx, __nv_bfloat16 *gz, float *gWp,
+                           float *gbp, int64_t P, int C, int Fo)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    constexpr int kMaxFo = 16, kMaxCL = 8;
+    float accW[kMaxFo][kMaxCL];
+    float accB[kMaxFo];
+    for (int o = 0; o < kMaxFo; ++o) {
+        accB[o] = 0.f;
+        for (int j = 0; j < kMaxCL; ++j) accW[o][j] = 0.f;
+    }
+    for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
+        float go[kMaxFo];
+        for (int o = 0; o < Fo; ++o) {
+            go[o] = gout[p * Fo + o];
+            accB[o] += go[o];
+        }
+        for (int j = 0; j < C / 32; ++j) {
+            const int c = lane + 32 * j;
+            const float xv = __bfloat162float(x[p * C + c]);
+            float g = 0.f;
+            for (int o = 0; o < Fo; ++o) {
+                g = fmaf(go[o], __ldg(Wp + o * C + c), g);
+                accW[o][j] = fmaf(go[o], xv, accW[o][j]);
+            }
+            gx[p * C + c] = g;
+            gz[p * C + c] = __float2bfloat16_rn(g * gelu_grad(__bfloat162float(z[p * C + c])));
+        }
+    }
+    for (int o = 0; o < Fo; ++o) {
+        for (int j = 0; j < C / 32; ++j) atomicAdd(&gWp[o * C + lane + 32 * j], accW[o][j]);
+        if (lane == 0) atomicAdd(&gbp[o], accB[o]);
+    }
+}
+
+// Lift backward: gWl[c][j] += sum_p gx0[p][c] feat[p][j]; gbl[c] += sum_p gx0[p][c].
+// Threads over channels, blocks over position ranges.
+__global__ void k_lift_bwd(const float *gx0, const float *feat, float *gWl, float *gbl, int64_t P,
+                           int F, int C, int64_t per_block)
+{
+    const int c = threadIdx.x;  // blockDim.x == C
+    constexpr int kMaxF = 64;
+    float acc[kMaxF];
+    for (int j = 0; j < kMaxF; ++j) acc[j] = 0.f;
+    float accb = 0.f;
+    const int64_t p0 = blockIdx.x * per_block, p1 = std::min(P, p0 + per_block);
+    for (int64_t p = p0; p < p1; ++p) {
+        const float g = gx0[p * C + c];
+        accb += g;
+        for (int j = 0; j < F; ++j) acc[j] = fmaf(g, __ldg(feat + p * F + j), acc[j]);
+    }
+    for (int j = 0; j < F; ++j) atomicAdd(&gWl[c * F + j], acc[j]);
+    atomicAdd(&gbl[c], accb);
+}
+
+// gb[c] += sum_p gz[p][c] (bf16 input), threads over channels
+__global__ void k_colsum(const __nv_bfloat16 *gz, float *gb, int64_t P, int C, int64_t per_block)
+{
+    const int64_t p0 = blockIdx.x * per_block, p1 = std::min(P, p0 + per_block);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float s = 0.f;
+        for (int64_t p = p0; p < p1; ++p) s += __bfloat162float(gz[p * C + c]);
+        atomicAdd(&gb[c], s);
+    }
+}
+
+// bf16 copies of the fp32 conv weights: W[t][co][ci] and WT[t][ci][co] = W[k-1-t][co][ci]
+__global__ void k_cast_weights(const float *w, __nv_bfloat16 *wb, __nv_bfloat16 *wt, int C, int k,
+                               int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t per_layer = (int64_t)k * C * C;
+        const int64_t layer = i / per_layer, r = i % per_layer;
+        const int t = (int)(r / ((int64_t)C * C)), co = (int)((r / C) % C), ci = (int)(r % C);
+        const __nv_bfloat16 v = __float2bfloat16_rn(w[i]);
+        wb[i] = v;
+        if (wt) wt[layer * per_layer + ((int64_t)(k - 1 - t) * C + ci) * C + co] = v;
+    }
+}
+
+__global__ void k_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1,
+                       float b2, float eps, float c1, float c2, float wd)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i] + wd * p[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+// loss partial sums (double) and gout = 2 (out - target) / n
+__global__ void k_mse(const float *out, const float *target, float *gout, double *loss, int64_t n)
+{
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = out[i] - target[i];
+        acc += (double)d * d;
+        if (gout) gout[i] = 2.0f * d / (float)n;
+    }
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        atomicAdd(loss, s / (double)n);
+    }
+}
+
+struct Scale4 { float s[4]; };
+struct Scale3 { float s[3]; };
+
+// feat[i] = ((rho-1)/s0, u/s1, (T-1)/s2, (gamma_b-1.4)/s3)
+__global__ void k_features(const float *rho, const float *u, const float *T, const float *gamma,
+                           float *feat, int64_t n, int L, Scale4 sc)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 f = make_float4((rho[i] - 1.0f) / sc.s[0], u[i] / sc.s[1], (T[i] - 1.0f) / sc.s[2],
+                                     (gamma[i / L] - 1.4f) / sc.s[3]);
+        reinterpret_cast<float4 *>(feat)[i] = f;
+    }
+}
+
+// target[i] = ((rho2-rho)/s0, (u2-u)/s1, (T2-T)/s2)
+__global__ void k_targets(const float *rho, const float *u, const float *T, const float *rho2,
+                          const float *u2, const float *T2, float *target, int64_t n, Scale3 sc)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        target[3 * i + 0] = (rho2[i] - rho[i]) / sc.s[0];
+        target[3 * i + 1] = (u2[i] - u[i]) / sc.s[1];
+        target[3 * i + 2] = (T2[i] - T[i]) / sc.s[2];
+    }
+}
+
+// (rho, u, T)_out = (rho, u, T) + out * scale
+__global__ void k_apply(const float *rho, const float *u, const float *T, const float *out,
+                        float *rho2, float *u2, float *T2, int64_t n, Scale3 sc)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        rho2[i] = rho[i] + out[3 * i + 0] * sc.s[0];
+        u2[i] = u[i] + out[3 * i + 1] * sc.s[1];
+        T2[i] = T[i] + out[3 * i + 2] * sc.s[2];
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+// One block per tube: conservation residual between two states (mass,
+// momentum scaled by mass, total energy with (1+n)/2 T) and, when a
+// reference is given, the L1 error (max over rho, u relative to the sound
+// speed, T).  Window [w0, w0 + W) of each tube of length L.
+__global__ void k_tube_checks(const float *rho, const float *u, const float *T, const float *rho2,
+                              const float *u2, const float *T2, const float *half_dof,
+                              const float *gamma, float *residual, float *l1, int L, int w0, int W)
+{
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    const double cv = half_dof ? (double)half_dof[b] : 0.0;  // only read when residual is asked for
+    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int l = w0 + threadIdx.x; l < w0 + W; l += blockDim.x) {
+        const int64_t i = (int64_t)b * L + l;
+        const double r1 = rho[i], v1 = u[i], t1 = T[i], r2 = rho2[i], v2 = u2[i], t2 = T2[i];
+        s[0] += r1;
+        s[1] += r1 * v1;
+        s[2] += r1 * (cv * t1 + 0.5 * v1 * v1);
+        s[3] += r2;
+        s[4] += r2 * v2;
+        s[5] += r2 * (cv * t2 + 0.5 * v2 * v2);
+        s[6] += fabs(r1 - r2);
+        s[7] += fabs(v1 - v2);
+        s[8] += fabs(t1 - t2);
+    }
+    double tot[9];
+    for (int q = 0; q < 9; ++q) tot[q] = block_sum(s[q], red);
+    // sound-speed and temperature sums of the reference (second) state
+    double cs = 0.0, ts = 0.0;
+    if (l1) {
+        const double g = gamma[b];
+        for (int l = w0 + threadIdx.x; l < w0 + W; l += blockDim.x) {
+            const int64_t i = (int64_t)b * L + l;
+            cs += sqrt(g * (double)T2[i]);
+            ts += fabs((double)T2[i]);
+        }
+        cs = block_sum(cs, red);
+        ts = block_sum(ts, red);
+    }
+    if (threadIdx.x == 0) {
+        if (residual) {
+            const double m = fabs(tot[3] - tot[0]) / tot[0];
+            const double j = fabs(tot[4] - tot[1]) / tot[0];
+            const double e = fabs(tot[5] - tot[2]) / tot[2];
+            residual[b] = (float)fmax(m, fmax(j, e));
+        }
+        if (l1) {
+            const double er = tot[6] / fabs(tot[3]);
+            const double eu = tot[7] / cs;
+            const double et = tot[8] / ts;
+            l1[b] = (float)fmax(er, fmax(eu, et));
+        }
+    }
+}
+
+// dst_f[i][w] = src_f[rows[i] * row_len + off[i] + w] for the three fields
+// (scatter: the reverse assignment).  One block row per (i, chunk of w).
+template <bool SCATTER>
+__global__ void k_rows(const float *a, const float *b, const float *c, float *da, float *db,
+                       float *dc, const int64_t *rows, const int *off, int count, int64_t row_len,
+                       int W)
+{
+    const int64_t n = (int64_t)count * W;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / W), w = (int)(e % W);
+        const int64_t g = rows[i] * row_len + (off ? off[i] : 0) + w;
+        if (SCATTER) {
+            da[g] = a[e];
+            db[g] = b[e];
+            dc[g] = c[e];
+        } else {
+            da[e] = a[g];
+            db[e] = b[g];
+            dc[e] = c[g];
+        }
+    }
+}
+
+// ------------------------------------------------------------ host helpers
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// [B][L][C] bf16, box (64 channels, rows positions, 1 tube), 128-byte swizzle
+bool map_act(CUtensorMap *m, const void *ptr, int B, int L, int C, int rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)L, (cuuint64_t)B};
+    const cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)L * C * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kChunk, (cuuint32_t)rows, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// [k*C][C] bf16 weights, box (64 input channels, 128 output rows)
+bool map_w(CUtensorMap *m, const void *ptr, int C, int k)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)k * C};
+    const cuuint64_t strides[1] = {(cuuint64_t)C * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)kTile};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+int set_smem_attrs()
+{
+    // once per device: the dynamic shared-memory limit of the three kernels
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LBM_ECUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return LBM_OK;
+    if (cudaFuncSetAttribute(k_conv_tc<kEpiForward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_tc<kEpiInputGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
+            cudaSuccess)
+        return LBM_ECUDA;
+    done[dev] = true;
+    return LBM_OK;
+}
+
+int launched(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+
+bool conv_shape_ok(int B, int L, int C, int k, int dil, int impl)
+{
+    if (B < 1 || B > 65535 || L < 1 || C < 128 || C % 128 != 0 || k < 1 || k % 2 == 0 || dil < 1)
+        return false;
+    if ((int64_t)(k / 2) * dil >= (1 << 20) || (int64_t)B * L * C >= (1ll << 40)) return false;
+    if (impl == 1) return k <= kSimtMaxK && (k - 1) * dil <= kSimtMaxSpan - kSimtTX;
+    return impl == 0 && (int64_t)k * C <= (1 << 20);
+}
+
+int conv_common(int epi, const void *in, const void *w, const ConvArgs &a, int impl, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (impl == 1) {
+        const dim3 grid((a.L + kSimtTX - 1) / kSimtTX, a.C / kSimtTC, a.B);
+        if (epi == kEpiForward)
+            k_conv_simt<kEpiForward><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)in,
+                                                          (const __nv_bfloat16 *)w, a);
+        else
+            k_conv_simt<kEpiInputGrad><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)in,
+                                                            (const __nv_bfloat16 *)w, a);
+        return launched(cudaGetLastError());
+    }
+    if (!aligned16(in) || !aligned16(w)) return LBM_EINVAL;
+    int rc = set_smem_attrs();
+    if (rc != LBM_OK) return rc;
+    CUtensorMap ma, mw;
+    if (!map_act(&ma, in, a.B, a.L, a.C, kTile) || !map_w(&mw, w, a.C, a.k)) return LBM_ECUDA;
+    const dim3 grid((a.L + kTile - 1) / kTile, a.C / kTile, a.B);
+    if (epi == kEpiForward)
+        k_conv_tc<kEpiForward><<<grid, 128, kSmemBytes, s>>>(ma, mw, a);
+    else
+        k_conv_tc<kEpiInputGrad><<<grid, 128, kSmemBytes, s>>>(ma, mw, a);
+    return launched(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_nn_conv_forward(const void *x, const void *w, const float *bias, void *y, void *z, int B,
+                        int L, int C, int k, int dil, int impl, int *status, void *stream)
+{
+    if (!x || !w || !bias || !y || !conv_shape_ok(B, L, C, k, dil, impl) || x == y) return LBM_EINVAL;
+    if (!aligned16(y) || (z && !aligned16(z))) return LBM_EINVAL;
+    ConvArgs a{};
+    a.B = B, a.L = L, a.C = C, a.k = k, a.dil = dil;
+    a.x = (const __nv_bfloat16 *)x;
+    a.bias = bias;
+    a.y = (__nv_bfloat16 *)y;
+    a.z = (__nv_bfloat16 *)z;
+    a.status = status;
+    return conv_common(kEpiForward, x, w, a, impl, stream);
+}
+
+int lbm_nn_conv_backward_data(const void *gz, const void *wt, float *gx, const void *zprev,
+                              void *gzprev, int B, int L, int C, int k, int dil, int impl,
+                              int *status, void *stream)
+{
+    if (!gz || !wt || !gx || !conv_shape_ok(B, L, C, k, dil, impl)) return LBM_EINVAL;
+    if ((zprev == nullptr) != (gzprev == nullptr) || gzprev == gz) return LBM_EINVAL;
+    if (!aligned16(gx) || (zprev && (!aligned16(zprev) || !aligned16(gzprev)))) return LBM_EINVAL;
+    ConvArgs a{};
+    a.B = B, a.L = L, a.C = C, a.k = k, a.dil = dil;
+    a.gx = gx;
+    a.zprev = (const __nv_bfloat16 *)zprev;
+    a.gzprev = (__nv_bfloat16 *)gzprev;
+    a.status = status;
+    return conv_common(kEpiInputGrad, gz, wt, a, impl, stream);
+}
+
+int lbm_nn_conv_backward_weight(const void *gz, const void *x, float *gw, int B, int L, int C, int k,
+                                int dil, int impl, int *status, void *stream)
+{
+    if (!gz || !x || !gw || !conv_shape_ok(B, L, C, k, dil, impl)) return LBM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (impl == 1) {
+        const dim3 grid((L + kSimtTX - 1) / kSimtTX, (C / kSimtTC) * (C / kSimtCI), B);
+        k_wgrad_simt<<<grid, 256, 0, s>>>((const __nv_bfloat16 *)gz, (const __nv_bfloat16 *)x, gw,
+                                          L, C, k, dil);
+        return launched(cudaGetLastError());
+    }
+    if (!aligned16(gz) || !aligned16(x) || !aligned16(gw)) return LBM_EINVAL;
+    int rc = set_smem_attrs();
+    if (rc != LBM_OK) return rc;
+    CUtensorMap mg, mx;
+    if (!map_act(&mg, gz, B, L, C, kWgRows) || !map_act(&mx, x, B, L, C, kWgRows)) return LBM_ECUDA;
+    const int tiles = (C / kTile) * (C / kTile) * k;
+    const int64_t total = (int64_t)B * ((L + kWgRows - 1) / kWgRows);
+    // about two resident blocks per SM in one wave
+    const int64_t want = std::max<int64_t>(1, (2 * 152 + tiles - 1) / tiles);
+    const int per_block = (int)std::max<int64_t>(1, (total + want - 1) / want);
+    const int chunks = (int)((total + per_block - 1) / per_block);
+    k_wgrad_tc<<<dim3(chunks, tiles), 128, kSmemBytes, s>>>(mg, mx, gw, B, L, C, k, dil, per_block,
+                                                            status);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_cast_weights(const float *w, void *w_bf16, void *wt_bf16, int layers, int C, int k,
+                        void *stream)
+{
+    if (!w || !w_bf16 || layers < 1 || C < 1 || k < 1) return LBM_EINVAL;
+    const int64_t n = (int64_t)layers * k * C * C;
+    k_cast_weights<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(w, (__nv_bfloat16 *)w_bf16,
+                                                                  (__nv_bfloat16 *)wt_bf16, C, k, n);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_lift(const float *feat, const float *Wl, const float *bl, void *x0, int64_t P, int F,
+                int C, void *stream)
+{
+    if (!feat || !Wl || !bl || !x0 || P < 1 || F < 1 || F > 64 || C < 1 || C > 256 ||
+        (size_t)(C * F + C) * sizeof(float) > 48 * 1024)
+        return LBM_EINVAL;
+    const size_t sh = (size_t)(C * F + C) * sizeof(float);
+    k_lift<<<grid_for(P * C), 256, sh, (cudaStream_t)stream>>>(feat, Wl, bl, (__nv_bfloat16 *)x0, P,
+                                                               F, C);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_lift_backward(const float *gx0, const float *feat, float *gWl, float *gbl, int64_t P,
+                         int F, int C, void *stream)
+{
+    if (!gx0 || !feat || !gWl || !gbl || P < 1 || F < 1 || F > 64 || C < 32 || C > 1024 || C % 32)
+        return LBM_EINVAL;
+    const int64_t per_block = std::max<int64_t>(64, (P + 1215) / 1216);
+    const int blocks = (int)((P + per_block - 1) / per_block);
+    k_lift_bwd<<<blocks, C, 0, (cudaStream_t)stream>>>(gx0, feat, gWl, gbl, P, F, C, per_block);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_head(const void *x, const float *Wp, const float *bp, float *out, int64_t P, int C, int Fo,
+                void *stream)
+{
+    if (!x || !Wp || !bp || !out || P < 1 || C < 1 || Fo < 1 || Fo > 16) return LBM_EINVAL;
+    k_head<<<grid_for(P * 32), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)x, Wp, bp, out,
+                                                               P, C, Fo);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_head_backward(const float *gout, const void *x, const float *Wp, const void *z, float *gx,
+                         void *gz, float *gWp, float *gbp, int64_t P, int C, int Fo, void *stream)
+{
+    if (!gout || !x || !Wp || !z || !gx || !gz || !gWp || !gbp || P < 1 || C < 32 || C > 256 ||
+        C % 32 || Fo < 1 || Fo > 16)
+        return LBM_EINVAL;
+    k_head_bwd<<<std::min<int64_t>(grid_for(P * 32), 152 * 4), 256, 0, (cudaStream_t)stream>>>(
+        gout, (const __nv_bfloat16 *)x, Wp, (const __nv_bfloat16 *)z, gx, (__nv_bfloat16 *)gz, gWp,
+        gbp, P, C, Fo);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_bias_grad(const void *gz, float *gb, int64_t P, int C, void *stream)
+{
+    if (!gz || !gb || P < 1 || C < 1) return LBM_EINVAL;
+    const int64_t per_block = std::max<int64_t>(64, (P + 1215) / 1216);
+    const int blocks = (int)((P + per_block - 1) / per_block);
+    k_colsum<<<blocks, std::min(C, 256), 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)gz, gb, P,
+                                                                    C, per_block);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                float eps, int t, float weight_decay, void *stream)
+{
+    if (!p || !g || !m || !v || n < 1 || t < 1) return LBM_EINVAL;
+    const float c1 = (float)(1.0 / (1.0 - std::pow((double)b1, t)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow((double)b2, t)));
+    k_adam<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2,
+                                                          weight_decay);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_mse(const float *out, const float *target, float *gout, double *loss, int64_t n,
+               void *stream)
+{
+    if (!out || !target || !loss || n < 1) return LBM_EINVAL;
+    k_mse<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(out, target, gout, loss, n);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_features(const float *rho, const float *u, const float *T, const float *gamma, float *feat,
+                    int B, int L, const float *in_scale, void *stream)
+{
+    if (!rho || !u || !T || !gamma || !feat || !in_scale || B < 1 || L < 1 || !aligned16(feat))
+        return LBM_EINVAL;
+    Scale4 sc;
+    for (int i = 0; i < 4; ++i) sc.s[i] = in_scale[i];
+    const int64_t n = (int64_t)B * L;
+    k_features<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(rho, u, T, gamma, feat, n, L, sc);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_targets(const float *rho, const float *u, const float *T, const float *rho2,
+                   const float *u2, const float *T2, float *target, int64_t n,
+                   const float *out_scale, void *stream)
+{
+    if (!rho || !u || !T || !rho2 || !u2 || !T2 || !target || !out_scale || n < 1) return LBM_EINVAL;
+    Scale3 sc;
+    for (int i = 0; i < 3; ++i) sc.s[i] = out_scale[i];
+    k_targets<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(rho, u, T, rho2, u2, T2, target, n, sc);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_apply(const float *rho, const float *u, const float *T, const float *out, float *rho2,
+                 float *u2, float *T2, int64_t n, const float *out_scale, void *stream)
+{
+    if (!rho || !u || !T || !out || !rho2 || !u2 || !T2 || !out_scale || n < 1) return LBM_EINVAL;
+    Scale3 sc;
+    for (int i = 0; i < 3; ++i) sc.s[i] = out_scale[i];
+    k_apply<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(rho, u, T, out, rho2, u2, T2, n, sc);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_tube_checks(const float *rho, const float *u, const float *T, const float *rho2,
+                       const float *u2, const float *T2, const float *half_dof, const float *gamma,
+                       float *residual, float *l1, int B, int L, int w0, int W, void *stream)
+{
+    if (!rho || !u || !T || !rho2 || !u2 || !T2 || B < 1 || L < 1 || w0 < 0 || W < 1 ||
+        w0 + W > L || (!residual && !l1) || (residual && !half_dof) || (l1 && !gamma))
+        return LBM_EINVAL;
+    k_tube_checks<<<B, 256, 0, (cudaStream_t)stream>>>(rho, u, T, rho2, u2, T2, half_dof, gamma,
+                                                       residual, l1, L, w0, W);
+    return launched(cudaGetLastError());
+}
+
+
+int lbm_nn_gather(const float *a, const float *b, const float *c, const int64_t *rows,
+                  const int *offsets, int count, int64_t row_len, int W, float *da, float *db,
+                  float *dc, void *stream)
+{
+    if (!a || !b || !c || !rows || !da || !db || !dc || count < 1 || W < 1 || row_len < W)
+        return LBM_EINVAL;
+    k_rows<false><<<grid_for((int64_t)count * W), 256, 0, (cudaStream_t)stream>>>(
+        a, b, c, da, db, dc, rows, offsets, count, row_len, W);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_scatter(const float *a, const float *b, const float *c, const int64_t *rows,
+                   const int *offsets, int count, int64_t row_len, int W, float *da, float *db,
+                   float *dc, void *stream)
+{
+    if (!a || !b || !c || !rows || !da || !db || !dc || count < 1 || W < 1 || row_len < W)
+        return LBM_EINVAL;
+    k_rows<true><<<grid_for((int64_t)count * W), 256, 0, (cudaStream_t)stream>>>(
+        a, b, c, da, db, dc, rows, offsets, count, row_len, W);
+    return launched(cudaGetLastError());
+}
+
+}  // extern "C"

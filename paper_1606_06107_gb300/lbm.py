@@ -71,6 +71,35 @@ SIGNATURES = {
     "lbm_batch_launch_count": (_i64, [_vp]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_batch_destroy": (None, [_vp]),
+    # learned surrogate (include/lbm.h, lbm_nn_*)
+    "lbm_nn_conv_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp] + [ctypes.c_int] * 6
+                            + [_vp, _vp]),
+    "lbm_nn_conv_backward_data": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp] + [ctypes.c_int] * 6
+                                  + [_vp, _vp]),
+    "lbm_nn_conv_backward_weight": (ctypes.c_int, [_vp, _vp, _vp] + [ctypes.c_int] * 6
+                                    + [_vp, _vp]),
+    "lbm_nn_cast_weights": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, _vp]),
+    "lbm_nn_lift": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_int, ctypes.c_int, _vp]),
+    "lbm_nn_lift_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_int,
+                                            ctypes.c_int, _vp]),
+    "lbm_nn_head": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_int, ctypes.c_int, _vp]),
+    "lbm_nn_head_backward": (ctypes.c_int, [_vp] * 8 + [_i64, ctypes.c_int, ctypes.c_int,
+                                                        _vp]),
+    "lbm_nn_bias_grad": (ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp]),
+    "lbm_nn_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, ctypes.c_int,
+                                   ctypes.c_float, _vp]),
+    "lbm_nn_mse": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp]),
+    "lbm_nn_features": (ctypes.c_int, [_vp] * 5 + [ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_float), _vp]),
+    "lbm_nn_targets": (ctypes.c_int, [_vp] * 7 + [_i64, ctypes.POINTER(ctypes.c_float), _vp]),
+    "lbm_nn_apply": (ctypes.c_int, [_vp] * 7 + [_i64, ctypes.POINTER(ctypes.c_float), _vp]),
+    "lbm_nn_tube_checks": (ctypes.c_int, [_vp] * 10 + [ctypes.c_int] * 4 + [_vp]),
+    "lbm_nn_gather": (ctypes.c_int, [_vp] * 5 + [ctypes.c_int, _i64, ctypes.c_int]
+                      + [_vp] * 4),
+    "lbm_nn_scatter": (ctypes.c_int, [_vp] * 5 + [ctypes.c_int, _i64, ctypes.c_int]
+                       + [_vp] * 4),
 }
 
 

@@ -173,3 +173,22 @@ def batched_tubes(count: int = 4096, seed: int = 0, lmin: int = 256, lmax: int =
         out.append(Workload(f"tube{k}", "D1Q7", int(ns[k]), float(taus[k]), (X,),
                             ("copy",), rho, u[None], T, steps))
     return out
+
+
+def surrogate_tubes(count: int = 1024, L: int = 4096, seed: int = 0, tau: float = 0.8,
+                    steps: int = 4000):
+    """Tubes for the learned surrogate, drawn like ``batched_tubes`` but all of
+    length L and with one relaxation time (the network's inputs are rho, u,
+    T and gamma only, so tau is a property of the operator it learns):
+    gamma from {5/3, 1.4, 9/7, 1.25}, left rho=1, p=1; right density
+    1/U[1, 10], pressure 1/logU[2, 100]; diaphragm at mid-tube; copy ends."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = rng.choice(np.array([2, 4, 6, 7]), count)
+    pr = np.exp(rng.uniform(np.log(2.0), np.log(100.0), count))
+    dr = rng.uniform(1.0, 10.0, count)
+    out = []
+    for k in range(count):
+        rho, u, T = _two_state_1d(L, (1.0, 0.0, 1.0), (1.0 / dr[k], 0.0, 1.0 / pr[k]))
+        out.append(Workload(f"stube{k}", "D1Q7", int(ns[k]), float(tau), (L,), ("copy",), rho,
+                            u[None], T, steps))
+    return out

@@ -1,0 +1,327 @@
+"""The learned surrogate's kernels (lbm_nn_*) against the FP64 NumPy reference
+of the network (oracle/surrogate_ref.py): each convolution product on the
+tensor cores and on the CUDA cores, the whole network's output and
+gradients, the data kernels, and the runtime's checks and fallback against
+the lattice Boltzmann solver."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import surrogate_ref as S
+
+pytestmark = pytest.mark.gpu
+
+BF16_ULP = 2.0 ** -7   # bfloat16 spacing at the start of a binade
+
+
+def _t():
+    import torch
+    return torch
+
+
+def bf16(a):
+    torch = _t()
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).cuda()
+
+
+def f32(a):
+    torch = _t()
+    return torch.tensor(np.asarray(a, np.float32)).cuda()
+
+
+def host(x):
+    return x.float().cpu().numpy().astype(np.float64)
+
+
+def vp(x):
+    return ctypes.c_void_p(0 if x is None else x.data_ptr())
+
+
+def stream():
+    return _t().cuda.current_stream().cuda_stream
+
+
+CONV_CASES = [  # (B, L, C, k, dil)
+    (3, 300, 128, 5, 3),
+    (2, 128, 128, 5, 1),
+    (1, 77, 256, 3, 2),
+    (2, 515, 128, 7, 4),
+]
+
+
+@pytest.mark.parametrize("impl", [0, 1])
+@pytest.mark.parametrize("case", CONV_CASES)
+def test_conv_forward(lbmlib, impl, case):
+    B, L, C, k, d = case
+    rng = np.random.default_rng(hash(case) % 2 ** 31)
+    x = S.bf16_round(rng.normal(0, 1, (B, L, C)))
+    W = S.bf16_round(rng.normal(0, 1 / np.sqrt(k * C), (k, C, C)))
+    b = rng.normal(0, 0.1, C)
+    xg, Wg = bf16(x), bf16(W)
+    y, z = bf16(np.zeros((B, L, C))), bf16(np.zeros((B, L, C)))
+    bg = f32(b)
+    st = _t().zeros(1, dtype=_t().int32, device="cuda")
+    rc = lbmlib.lbm_nn_conv_forward(vp(xg), vp(Wg), vp(bg), vp(y), vp(z), B, L, C, k, d, impl,
+                                    vp(st), stream())
+    assert rc == 0
+    _t().cuda.synchronize()
+    assert int(st.item()) == 0
+    zr = S.conv1d(x, W, d) + b
+    terms = S.conv1d(np.abs(x), np.abs(W), d) + np.abs(b)
+    # the kernel rounds its float32 sum once to bfloat16
+    err = np.abs(host(z) - zr)
+    assert np.all(err <= BF16_ULP * np.abs(zr) * 0.5 + 1e-5 * terms + 1e-30), err.max()
+    yr = x + S.gelu(zr)
+    erry = np.abs(host(y) - yr)
+    assert np.all(erry <= BF16_ULP * np.abs(yr) * 0.5 + 2e-5 * terms + 1e-30), erry.max()
+
+
+@pytest.mark.parametrize("impl", [0, 1])
+@pytest.mark.parametrize("case", CONV_CASES)
+def test_conv_backward_data(lbmlib, impl, case):
+    B, L, C, k, d = case
+    torch = _t()
+    rng = np.random.default_rng(1 + hash(case) % 2 ** 31)
+    gz = S.bf16_round(rng.normal(0, 1, (B, L, C)))
+    W = rng.normal(0, 1 / np.sqrt(k * C), (k, C, C))
+    Wr = S.bf16_round(W)
+    gx0 = rng.normal(0, 1, (B, L, C))
+    zprev = S.bf16_round(rng.normal(0, 1.5, (B, L, C)))
+    wb = torch.empty(k * C * C, dtype=torch.bfloat16, device="cuda")
+    wt = torch.empty_like(wb)
+    Wf = f32(W)
+    assert lbmlib.lbm_nn_cast_weights(vp(Wf), vp(wb), vp(wt), 1, C, k, stream()) == 0
+    gx = f32(gx0)
+    gzp = bf16(np.zeros((B, L, C)))
+    gzg, zpg = bf16(gz), bf16(zprev)   # kept alive across the call
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lbmlib.lbm_nn_conv_backward_data(vp(gzg), vp(wt), vp(gx), vp(zpg), vp(gzp),
+                                          B, L, C, k, d, impl, vp(st), stream())
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    np.testing.assert_array_equal(host(wb).reshape(k, C, C), Wr)
+    ref = np.float32(gx0).astype(np.float64) + S.conv1d_input_grad(gz, Wr, d)
+    terms = S.conv1d_input_grad(np.abs(gz), np.abs(Wr), d)
+    err = np.abs(host(gx) - ref)
+    assert np.all(err <= 1e-5 * (terms + np.abs(ref)) + 1e-30), err.max()
+    gzr = ref * S.gelu_grad(zprev)
+    errz = np.abs(host(gzp) - gzr)
+    assert np.all(errz <= BF16_ULP * np.abs(gzr) * 0.5 + 2e-5 * (terms + np.abs(ref)) + 1e-30)
+
+
+@pytest.mark.parametrize("impl", [0, 1])
+@pytest.mark.parametrize("case", CONV_CASES)
+def test_conv_backward_weight(lbmlib, impl, case):
+    B, L, C, k, d = case
+    torch = _t()
+    rng = np.random.default_rng(2 + hash(case) % 2 ** 31)
+    gz = S.bf16_round(rng.normal(0, 1, (B, L, C)))
+    x = S.bf16_round(rng.normal(0, 1, (B, L, C)))
+    gw = torch.ones(k * C * C, dtype=torch.float32, device="cuda")   # accumulates
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gzg, xg = bf16(gz), bf16(x)   # kept alive across the call
+    rc = lbmlib.lbm_nn_conv_backward_weight(vp(gzg), vp(xg), vp(gw), B, L, C, k, d, impl,
+                                            vp(st), stream())
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = 1.0 + S.conv1d_weight_grad(gz, x, k, d)
+    terms = S.conv1d_weight_grad(np.abs(gz), np.abs(x), k, d)
+    err = np.abs(host(gw).reshape(k, C, C) - ref)
+    assert np.all(err <= 1e-5 * terms + 2e-7 * np.abs(ref)), err.max()
+
+
+def test_conv_rejects_bad_arguments(lbmlib):
+    torch = _t()
+    x = torch.zeros(2 * 64 * 128, dtype=torch.bfloat16, device="cuda")
+    w = torch.zeros(5 * 128 * 128, dtype=torch.bfloat16, device="cuda")
+    b = torch.zeros(128, dtype=torch.float32, device="cuda")
+    y = torch.zeros_like(x)
+    s = stream()
+    ok = lbmlib.lbm_nn_conv_forward
+    assert ok(vp(x), vp(w), vp(b), vp(y), None, 2, 64, 96, 5, 1, 0, None, s) == -1   # C % 128
+    assert ok(vp(x), vp(w), vp(b), vp(y), None, 2, 64, 128, 4, 1, 0, None, s) == -1  # even k
+    assert ok(vp(x), vp(w), vp(b), vp(x), None, 2, 64, 128, 5, 1, 0, None, s) == -1  # x == y
+    assert ok(vp(x), vp(w), vp(b), vp(y), None, 2, 64, 128, 5, 1, 2, None, s) == -1  # impl
+    off = ctypes.c_void_p(x.data_ptr() + 2)                                         # alignment
+    assert ok(off, vp(w), vp(b), vp(y), None, 1, 64, 128, 5, 1, 0, None, s) == -1
+
+
+def small_net(patch=1, dil=(1, 2, 4), C=128, seed=3):
+    from paper_1606_06107_gb300.surrogate import ConvOperator
+    net = ConvOperator(C=C, k=5, dilations=dil, patch=patch, seed=seed)
+    rng = np.random.default_rng(seed)
+    p = S.init_params(C=C, k=5, dil=dil, seed=seed)
+    arrays = [rng.normal(0, 1 / np.sqrt(4 * patch), (C, 4 * patch)), rng.normal(0, 0.2, C)]
+    arrays += [w * 6 for w in p.W] + [rng.normal(0, 0.2, C) for _ in dil]
+    arrays += [rng.normal(0, 0.3 / np.sqrt(C), (3 * patch, C)), rng.normal(0, 0.1, 3 * patch)]
+    net.set_params(arrays)
+    return net, arrays
+
+
+def oracle_params(arrays, dil, C=128):
+    N = len(dil)
+    return S.Params(arrays[0], arrays[1], list(arrays[2:2 + N]), list(arrays[2 + N:2 + 2 * N]),
+                    arrays[2 + 2 * N], arrays[3 + 2 * N], list(dil))
+
+
+@pytest.mark.parametrize("patch,impl", [(1, 0), (2, 0), (1, 1)])
+def test_network_output_and_gradients(lbmlib, patch, impl):
+    """Loss, output and every gradient block of a 3-layer network against
+    the FP64 reference, which rounds to bfloat16 where the kernels do."""
+    torch = _t()
+    dil = (1, 2, 4)
+    net, arrays = small_net(patch=patch, dil=dil)
+    net.impl = impl
+    B, L = 2, 400
+    rng = np.random.default_rng(9)
+    feat = rng.normal(0, 1, (B, L, 4))
+    target = rng.normal(0, 0.5, (B, L, 3))
+    fg, tg = f32(feat).reshape(-1), f32(target).reshape(-1)
+    loss = net.loss_and_grad(fg, tg, B, L)
+    torch.cuda.synchronize()
+    net.check_status()
+    out = host(net._buffers(B, L // patch, True)["out"]).reshape(B, L // patch, 3 * patch)
+    p = oracle_params([np.asarray(a, np.float32).astype(np.float64) for a in arrays], dil)
+    a = np.float32(feat).astype(np.float64).reshape(B, L // patch, 4 * patch)
+    tref = np.float32(target).astype(np.float64).reshape(B, L // patch, 3 * patch)
+    oref, cache = S.forward(p, a)
+    lref, gout = S.mse(oref, tref)
+    grads_ref = S.backward(p, cache, gout)
+    # Both sides round to bfloat16 at the same points; a float32 and a double
+    # sum that straddle a rounding boundary differ by one bfloat16 ulp there,
+    # which the next layers carry (measured: output 1.3e-3 of its scale,
+    # gradients 5e-4 relative, loss 1e-5).
+    scale = np.abs(oref).max()
+    assert np.abs(out - oref).max() <= 5e-3 * scale
+    assert abs(float(loss.item()) - lref) <= 1e-3 * lref
+    for g, r in zip(net.get_grads(), grads_ref):
+        rel = np.linalg.norm(g - r) / np.linalg.norm(r)
+        assert rel <= 3e-3, (g.shape, rel)
+
+
+def test_data_kernels(lbmlib):
+    torch = _t()
+    from paper_1606_06107_gb300.surrogate import ConvOperator, _rows, _scatter
+    net = ConvOperator(C=128, dilations=(1,), in_scale=(0.5, 2.0, 0.25, 0.25),
+                       out_scale=(1e-2, 2e-2, 3e-2))
+    rng = np.random.default_rng(4)
+    B, L = 3, 50
+    rho, u, T = 1 + 0.2 * rng.random((B, L)), rng.normal(0, 0.3, (B, L)), 1 + rng.random((B, L))
+    gam = np.array([5 / 3, 1.4, 1.25])
+    g = [f32(v).reshape(-1) for v in (rho, u, T)]
+    gg0 = f32(gam)
+    feat = host(net.features(*g, gg0, B, L)).reshape(B, L, 4)
+    ref = S.features(*(np.float32(v).astype(np.float64) for v in (rho, u, T)), np.float32(gam),
+                     (0.5, 2.0, 0.25, 0.25))
+    np.testing.assert_allclose(feat, ref, rtol=2e-6, atol=1e-7)
+    rho2, u2, T2 = rho + 0.01, u - 0.02, T * 1.01
+    g2 = [f32(v).reshape(-1) for v in (rho2, u2, T2)]
+    tgt = host(net.targets(*g, *g2)).reshape(B, L, 3)
+    np.testing.assert_allclose(tgt[..., 0], (np.float32(rho2) - np.float32(rho)) / 1e-2, rtol=1e-5,
+                               atol=1e-4)
+    # gather a window of rows 2 and 0, scatter it back into zeros
+    rows = torch.tensor([2, 0], dtype=torch.int64, device="cuda")
+    offs = torch.tensor([5, 11], dtype=torch.int32, device="cuda")
+    win = _rows(net.lib, torch, net.device, g, rows, offs, 20, L)
+    np.testing.assert_array_equal(host(win[0]).reshape(2, 20),
+                                  np.float32(np.stack([rho[2, 5:25], rho[0, 11:31]])))
+    dst = [torch.zeros(B * L, dtype=torch.float32, device="cuda") for _ in range(3)]
+    _scatter(net.lib, torch, net.device, win, rows, offs, 20, L, dst)
+    back = host(dst[1]).reshape(B, L)
+    assert np.array_equal(back[2, 5:25], np.float32(u[2, 5:25])) and back[1].sum() == 0
+    # residual and L1 checks against the reference definitions
+    res = torch.empty(B, dtype=torch.float32, device="cuda")
+    l1 = torch.empty(B, dtype=torch.float32, device="cuda")
+    n = np.array([2, 4, 7])
+    hd, gg = f32((1 + n) / 2.0), f32(gam)
+    rc = net.lib.lbm_nn_tube_checks(*(vp(x) for x in g + g2), vp(hd), vp(gg), vp(res), vp(l1),
+                                    B, L, 0, L, stream())
+    assert rc == 0
+    r32 = [np.float32(v).astype(np.float64) for v in (rho, u, T, rho2, u2, T2)]
+    np.testing.assert_allclose(host(res), S.conservation_residual(*r32, n), rtol=1e-5)
+    np.testing.assert_allclose(host(l1), S.l1_error(*r32[:3], *r32[3:], np.float32(gam)),
+                               rtol=1e-5)
+
+
+def _tubes(B, L, seed):
+    from paper_1606_06107_gb300 import workloads
+    wls = workloads.surrogate_tubes(count=B, L=L, seed=seed)
+    return (np.concatenate([w.rho for w in wls]), np.concatenate([w.u[0] for w in wls]),
+            np.concatenate([w.T for w in wls]), np.array([w.n for w in wls]), wls[0].tau)
+
+
+def test_spot_window_equals_full_tube_method(lbmlib):
+    """The method on a window with a 2K-node margin reproduces the full-tube
+    run bit for bit in the window's interior (the FD stencil reaches two
+    nodes per step)."""
+    torch = _t()
+    from paper_1606_06107_gb300 import LbmBatch
+    B, L, K = 3, 512, 32
+    rho, u, T, n, tau = _tubes(B, L, 5)
+    full = LbmBatch([L] * B, n, [tau] * B)
+    full.set_macro(rho, u, T)
+    full.run(K)
+    ref = [host(x).reshape(B, L) for x in full.moments()]
+    off, W = 200, 100
+    M = 2 * K
+    sl = slice(off - M, off + W + M)
+    win = LbmBatch([W + 2 * M] * B, n, [tau] * B)
+    win.set_macro(rho.reshape(B, L)[:, sl].ravel(), u.reshape(B, L)[:, sl].ravel(),
+                  T.reshape(B, L)[:, sl].ravel())
+    win.run(K)
+    got = [host(x).reshape(B, W + 2 * M)[:, M:M + W] for x in win.moments()]
+    for a, r in zip(got, ref):
+        np.testing.assert_array_equal(a, r[:, off:off + W])
+
+
+def test_runner_falls_back_to_the_method(lbmlib):
+    """An untrained network fails its checks everywhere; every tube is then
+    recomputed by the method and the call returns exactly L_K(state)."""
+    torch = _t()
+    from paper_1606_06107_gb300 import LbmBatch
+    from paper_1606_06107_gb300.surrogate import ConvOperator, SurrogateRunner
+    B, L, K = 4, 512, 32
+    rho, u, T, n, tau = _tubes(B, L, 6)
+    net = ConvOperator(C=128, dilations=(1, 2), out_scale=(1.0, 1.0, 1.0), seed=1)
+    # a constant head output of 0.3 per channel: the prediction is far from the method
+    arrays = net.get_params()
+    arrays[-2] = np.zeros_like(arrays[-2])
+    arrays[-1] = np.array([0.3, 0.3, 0.3])
+    net.set_params(arrays)
+    run = SurrogateRunner(net, n, tau, L, K)
+    g = [f32(v) for v in (rho, u, T)]
+    (r2, u2, T2), fb = run.advance(*g)
+    assert sorted(fb.tolist()) == list(range(B))
+    lb = LbmBatch([L] * B, n, [tau] * B)
+    lb.set_macro(rho, u, T)
+    lb.run(K)
+    for a, r in zip((r2, u2, T2), lb.moments()):
+        np.testing.assert_array_equal(host(a), host(r))
+    # with an infinite tolerance nothing falls back and the prediction stands
+    run_inf = SurrogateRunner(net, n, tau, L, K, tol=np.inf)
+    (r3, _, _), fb = run_inf.advance(*g)
+    assert fb.size == 0
+    np.testing.assert_allclose(host(r3), np.float32(rho) + np.float32(0.3), rtol=1e-6)
+
+
+def test_training_reduces_the_loss(lbmlib):
+    """A few hundred Adam steps on restarted-method pairs of 8 tubes lower the
+    loss by a large factor (the network learns, on the GPU kernels alone)."""
+    torch = _t()
+    from paper_1606_06107_gb300.surrogate import (ConvOperator, Trainer, output_scales,
+                                                  restarted_trajectories)
+    B, L, K = 8, 512, 32
+    rho, u, T, n, tau = _tubes(B, L, 7)
+    tr = restarted_trajectories(rho, u, T, n, tau, L, K, windows=12)
+    assert tr.ok.sum() >= 6
+    net = ConvOperator(C=128, dilations=(1, 2, 4, 1), out_scale=output_scales(tr), seed=2)
+    trainer = Trainer(net, tr, batch=8, seed=0)
+    first = [float(trainer.step(1e-3).item()) for _ in range(5)]
+    for i in range(300):
+        loss = trainer.step(1e-3)
+    last = [float(trainer.step(3e-4).item()) for _ in range(10)]
+    net.check_status()
+    assert np.mean(last) < 0.2 * np.mean(first), (first, last)
