@@ -48,6 +48,18 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def add_peak(roof):
+    """Complete a tensor-core roofline entry with the measured bf16 peak (burst:
+    the kernel is timed alone)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, kind = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    roof.update({"peak": peak, "frac": roof["achieved"] / peak, "peak_kind": kind,
+                 "traffic": None})
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -213,6 +225,250 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
             "rel_l1_vs_per_tube": worst}
 
 
+def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int = 4096,
+                  K: int = 32, windows: int = 125, train_seconds: float = 60.0, patch: int = 4,
+                  batch: int = 32, single_sample: int = 16, tol: float = 1e-2):
+    """The learned surrogate on 1-D tubes of L nodes (workloads.surrogate_tubes:
+    gamma in {5/3, 1.4, 9/7, 1.25}, pressure ratio log-U[2,100], density ratio
+    U[1,10], tau 0.8, FD transport m = 10).  Training pairs: restarted-method
+    trajectories of `train_tubes` tubes x `windows` windows of K steps (seed 0).
+    The network (~1M parameters, bf16 weights, fp32 accumulation on the tensor
+    cores) trains on the GPU for `train_seconds`; then `eval_tubes` held-out
+    tubes (seed 1) are advanced `windows` calls from their initial state by
+    the checked runner (conservation residual and a spot-check window against
+    the method on every tube, fallback above `tol`), and compared with the
+    restarted method's own trajectory.  Baselines per call: the single-instance
+    method (one lbm_handle per tube; a sample of `single_sample` tubes, scaled)
+    and the batched method (all tubes in one persistent launch)."""
+    import torch
+
+    from paper_1606_06107_gb300 import Lbm, LbmBatch, workloads
+    from paper_1606_06107_gb300.surrogate import (ConvOperator, SurrogateRunner, Trainer,
+                                                  cosine_lr, output_scales,
+                                                  restarted_trajectories)
+
+    def fields(count, seed):
+        wls = workloads.surrogate_tubes(count=count, L=L, seed=seed)
+        return ([np.concatenate([getattr(w, f) if f != "u" else w.u[0] for w in wls])
+                 for f in ("rho", "u", "T")], np.array([w.n for w in wls]), wls[0].tau)
+
+    stream = torch.cuda.current_stream()
+    t_gen = time.perf_counter()
+    (r, u, T), n_tr, tau = fields(train_tubes, 0)
+    tr = restarted_trajectories(r, u, T, n_tr, tau, L, K, windows, device=dev)
+    (r, u, T), n_ev, _ = fields(eval_tubes, 1)
+    ev = restarted_trajectories(r, u, T, n_ev, tau, L, K, windows, device=dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+
+    net = ConvOperator(C=128, k=5, patch=patch, out_scale=output_scales(tr), seed=0, device=dev)
+    trainer = Trainer(net, tr, batch=batch, seed=0)
+    trainer.run([0.0] * 10)                # capture the step graph; lr 0 leaves the weights
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    trainer.run([0.0] * 100)
+    torch.cuda.synchronize()
+    per_step = (time.perf_counter() - a) / 100
+    total = max(100, min(trainer.max_steps, int(train_seconds / per_step)))
+    net.set_params(net.initial_params(0))
+    trainer.reset()
+    a = time.perf_counter()
+    first = float(trainer.run([cosine_lr(0, total)]).item())
+    last = float(trainer.run([cosine_lr(i, total) for i in range(1, total)]).item())
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - a
+    net.check_status()
+
+    # tensor-core roofline of the forward convolution at the inference shape
+    Lp, C = L // patch, net.C
+    x = torch.randn(eval_tubes * Lp * C, device=dev).to(torch.bfloat16)
+    y = torch.empty_like(x)
+    from paper_1606_06107_gb300.surrogate import _fp
+    conv = lambda: net.lib.lbm_nn_conv_forward(_fp(x), net._wb(0), net._ptr(net.params, "b", 0),
+                                               _fp(y), None, eval_tubes, Lp, C, net.k, 2, 0,
+                                               _fp(net.status), stream.cuda_stream)
+    for _ in range(3):
+        conv()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(20):
+        conv()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    conv_ms = e0.elapsed_time(e1) / 20
+    conv_tflops = 2.0 * eval_tubes * Lp * C * C * net.k / (conv_ms * 1e-3) / 1e12
+    del x, y
+
+    # the network alone, no checks: rollout of the held-out tubes
+    B_ev = eval_tubes
+    gam_ev = torch.as_tensor(ev.gamma.astype(np.float32), device=dev)
+    alone = [f[0].clone() for f in (ev.rho, ev.u, ev.T)]
+    net.predict(*alone, gam_ev, B_ev, L)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for j in range(windows):
+        alone = list(net.predict(*alone, gam_ev, B_ev, L))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    net_ms = e0.elapsed_time(e1) / windows
+
+    # checked rollout of the held-out tubes
+    run = SurrogateRunner(net, n_ev, tau, L, K, tol=tol)
+    cur = [f[0].clone() for f in (ev.rho, ev.u, ev.T)]
+    run.advance(*cur)                     # warm-up (buffers, spot-check graph)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for j in range(windows):
+        cur, _ = run.advance(*cur)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sur_ms = e0.elapsed_time(e1) / windows
+    # one more pass with per-phase timing (not part of the timed region)
+    prof = SurrogateRunner(net, n_ev, tau, L, K, tol=tol, timing=True)
+    pc = [f[0].clone() for f in (ev.rho, ev.u, ev.T)]
+    for j in range(8):
+        pc, _ = prof.advance(*pc)
+    phases = {k: v / 8 for k, v in prof.times.items()}
+
+    def l1(state, j):
+        ref = [f[j].view(eval_tubes, L).double() for f in (ev.rho, ev.u, ev.T)]
+        got = [x.view(eval_tubes, L).double() for x in state]
+        g = torch.as_tensor(ev.gamma, dtype=torch.float64, device=dev)[:, None]
+        er = (got[0] - ref[0]).abs().sum(1) / ref[0].abs().sum(1)
+        eu = (got[1] - ref[1]).abs().sum(1) / torch.sqrt(g * ref[2]).sum(1)
+        eT = (got[2] - ref[2]).abs().sum(1) / ref[2].abs().sum(1)
+        return torch.maximum(er, torch.maximum(eu, eT)).cpu().numpy()
+
+    ok = ev.ok
+    e_all = l1(cur, windows)[ok]
+    finite = np.isfinite(e_all)
+    e_sur = e_all[finite]
+    e_net = l1(alone, windows)[ok]
+    net_finite = np.isfinite(e_net)
+    e_net = e_net[net_finite]
+    e_id = l1([f[0] for f in (ev.rho, ev.u, ev.T)], windows)[ok]
+    stats = dict(run.stats)
+
+    # baselines per call: batched method over all tubes, single instances on a sample
+    lb = LbmBatch([L] * eval_tubes, n_ev, [tau] * eval_tubes, mode="fd", m_fd=10, device=dev,
+                  stream=stream)
+    st0 = [f[10] for f in (ev.rho, ev.u, ev.T)]
+    lb.set_macro(*st0)
+    lb.run(K)
+    lb.moments()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(10):
+        lb.set_macro(*st0)
+        lb.run(K)
+        lb.moments()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1) / 10
+    pick = np.linspace(0, eval_tubes - 1, single_sample).astype(int)
+    sims = []
+    for b in pick:
+        sl = slice(int(b) * L, (int(b) + 1) * L)
+        s = Lbm("D1Q7", int(n_ev[b]), tau, (L,), ("copy",), mode="fd", m_fd=10, device=dev,
+                stream=stream)
+        sims.append((s, [f[sl] for f in st0]))
+    for s, f in sims:
+        s.set_macro(f[0], f[1][None], f[2]); s.step(K); s.moments()
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    for _ in range(3):
+        for s, f in sims:
+            s.set_macro(f[0], f[1][None], f[2]); s.step(K); s.moments()
+    torch.cuda.synchronize()
+    single_ms = (time.perf_counter() - a) / (3 * single_sample) * eval_tubes * 1e3
+    for s, _ in sims:
+        s.close()
+    q = lambda v, p: float(np.percentile(v, p)) if v.size else None
+    return {"metric": "surrogate speedup vs single-instance method at stated L1",
+            "value": single_ms / sur_ms, "unit": "x",
+            "config": f"{eval_tubes} held-out tubes x {L} nodes, K = {K} steps per call, "
+                      f"{windows} calls ({windows * K} steps) from the initial state",
+            "ms_per_call": sur_ms, "single_instance_ms_per_call": single_ms,
+            "batched_method_ms_per_call": batched_ms,
+            "ratio_vs_batched_method": batched_ms / sur_ms,
+            "stated_tol": tol,
+            "l1_vs_method_after_rollout": {"median": q(e_sur, 50), "p95": q(e_sur, 95),
+                                           "max": q(e_sur, 100), "tubes": int(ok.sum()),
+                                           "non_finite_tubes": int((~finite).sum())},
+            "network_alone": {"ms_per_call": net_ms,
+                              "l1_median": q(e_net, 50), "l1_p95": q(e_net, 95),
+                              "l1_max": q(e_net, 100),
+                              "non_finite_tubes": int((~net_finite).sum())},
+            "l1_identity_after_rollout": {"median": q(e_id, 50), "max": q(e_id, 100)},
+            "phase_ms_per_call": phases,
+            "fallback_tubes": stats["fallback_tubes"],
+            "fallback_fraction": stats["fallback_tubes"] / ((windows + 1) * eval_tubes),
+            "max_spot_l1": stats["max_l1"],
+            "training": {"pairs": int(train_tubes * windows), "steps": total,
+                         "batch_tubes": batch, "seconds": t_train, "cuda_graph": True,
+                         "ms_per_step": t_train / total * 1e3, "loss_first": first,
+                         "loss_last": last, "data_gen_seconds": t_gen},
+            "network": {"params": net.n_params, "channels": C, "taps": net.k,
+                        "layers": net.N, "dilations": list(net.dil), "patch": patch,
+                        "dtype": "bf16 weights/activations, fp32 accumulation"},
+            "roofline": {"bound": "tensor", "kernel": "k_conv_tcp<forward>",
+                         "achieved": conv_tflops, "unit": "TFLOP/s", "avg_launch_ms": conv_ms}}
+
+
+def conv_leg(dev, tubes: int = 1024, L: int = 4096, patch: int = 4, C: int = 128, k: int = 5,
+             dil: int = 2, reps: int = 20):
+    """The surrogate's three tensor-core convolution products alone, at the
+    inference shape (tubes x L/patch positions x C channels): forward with
+    the fused GELU/residual epilogue, input gradient with the fused
+    activation-derivative epilogue, and weight gradient; TFLOP/s of each
+    from CUDA events over `reps` launches (profiling runs)."""
+    import torch
+
+    from paper_1606_06107_gb300 import load_library
+    from paper_1606_06107_gb300.surrogate import _fp
+
+    lib = load_library()
+    stream = torch.cuda.current_stream().cuda_stream
+    Lp = L // patch
+    P = tubes * Lp
+    g = torch.Generator(device=dev).manual_seed(0)
+    x = torch.randn(P * C, device=dev, generator=g).to(torch.bfloat16)
+    z = torch.empty_like(x)
+    y = torch.empty_like(x)
+    w = (torch.randn(k * C * C, device=dev, generator=g) * 0.05).to(torch.bfloat16)
+    bias = torch.zeros(C, device=dev)
+    gx = torch.zeros(P * C, device=dev)
+    gw = torch.zeros(k * C * C, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    calls = {
+        "forward": lambda: lib.lbm_nn_conv_forward(_fp(x), _fp(w), _fp(bias), _fp(y), _fp(z), tubes,
+                                                   Lp, C, k, dil, 0, _fp(st), stream),
+        "input_grad": lambda: lib.lbm_nn_conv_backward_data(_fp(x), _fp(w), _fp(gx), _fp(z),
+                                                           _fp(y), tubes, Lp, C, k, dil, 0,
+                                                           _fp(st), stream),
+        "weight_grad": lambda: lib.lbm_nn_conv_backward_weight(_fp(x), _fp(y), _fp(gw), tubes, Lp,
+                                                              C, k, dil, 0, _fp(st), stream),
+    }
+    flops = 2.0 * P * C * C * k
+    out = {"shape": f"{tubes} tubes x {Lp} positions x {C} channels, k = {k}, dilation {dil}",
+           "flops_per_launch": flops}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, fn in calls.items():
+        for _ in range(3):
+            if fn() != 0:
+                raise RuntimeError(name)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+    if int(st.item()):
+        raise RuntimeError("tensor-core kernel timed out")
+    return out
+
+
 def blast_leg(dev, L: int = 384, steps: int = 10, storage: str = "f16", oracle_L: int = 32,
               oracle_steps: int = 50):
     """The 3-D blast workload on D3Q343: L^3 nodes, rho = 1, a central sphere
@@ -329,6 +585,14 @@ def run_gpu(args):
         if args.only == "batched":
             res = batched_leg(dev, steps=args.batched_steps, count=args.batched_count,
                               sample=min(48, args.batched_count))
+        elif args.only == "conv":
+            res = conv_leg(dev, tubes=args.surrogate_eval_tubes, patch=args.surrogate_patch)
+        elif args.only == "surrogate":
+            res = surrogate_leg(dev, train_tubes=args.surrogate_train_tubes,
+                                eval_tubes=args.surrogate_eval_tubes,
+                                windows=args.surrogate_windows,
+                                train_seconds=args.surrogate_seconds, patch=args.surrogate_patch)
+            add_peak(res["roofline"])
         else:
             res = blast_leg(dev, L=args.blast_size, steps=args.blast_steps,
                             oracle_L=min(16, args.blast_size), oracle_steps=5)
@@ -429,6 +693,14 @@ def run_gpu(args):
     blast = None
     if world == 1 and not args.no_blast:
         blast = blast_leg(dev, L=args.blast_size, steps=args.blast_steps)
+    surrogate = None
+    if world == 1 and not args.no_surrogate:
+        surrogate = surrogate_leg(dev, train_tubes=args.surrogate_train_tubes,
+                                  eval_tubes=args.surrogate_eval_tubes,
+                                  windows=args.surrogate_windows,
+                                  train_seconds=args.surrogate_seconds,
+                                  patch=args.surrogate_patch)
+        add_peak(surrogate["roofline"])
     cpu = None
     if world == 1 and not args.no_cpu:
         rate, steps, dt, threads = cpu_oracle_rate()
@@ -455,6 +727,7 @@ def run_gpu(args):
         "clocks": clocks.summary(),
         "batched": batched,
         "blast_3d": blast,
+        "surrogate": surrogate,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -474,8 +747,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the ensemble leg")
     ap.add_argument("--no-blast", action="store_true", help="skip the 3-D D3Q343 leg")
-    ap.add_argument("--only", default="all", choices=["all", "batched", "blast"],
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
+    ap.add_argument("--only", default="all", choices=["all", "batched", "blast", "surrogate", "conv"],
                     help="run one leg alone (profiling)")
+    ap.add_argument("--surrogate-train-tubes", type=int, default=1600)
+    ap.add_argument("--surrogate-eval-tubes", type=int, default=1024)
+    ap.add_argument("--surrogate-windows", type=int, default=125)
+    ap.add_argument("--surrogate-seconds", type=float, default=60.0)
+    ap.add_argument("--surrogate-patch", type=int, default=4)
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--batched-steps", type=int, default=4000)
     ap.add_argument("--blast-size", type=int, default=384)

@@ -82,8 +82,8 @@ enum lbm_status {
  * tau > 0 relaxation time in lattice steps (Eq. DisEvolI/EvoEtaJ).  The
  * lattice scaling factor r and weights (Tables I, II) are solved on the host
  * in double precision from the Gauss-Hermite moment equations and rounded
- * once to float.  Mode defaults to LBM_MODE_STREAM.  LBM_D3Q343 is not
- * supported by this version (LBM_EINVAL). */
+ * once to float.  Mode defaults to LBM_MODE_STREAM.  LBM_D3Q343 (D = 3, the
+ * tensor product D1Q7 x D1Q7 x D1Q7) runs in LBM_MODE_STREAM only. */
 int lbm_create(int D, int lattice, int n, double tau, lbm_handle *out);
 
 /* Select the transport mode (lbm_mode) and, for LBM_MODE_FD, the number m
@@ -220,6 +220,13 @@ typedef struct lbm_batch_ctx *lbm_batch;
 int lbm_batch_create(int count, const int64_t *lengths, const int *n, const double *tau,
                      int mode, int m_fd, lbm_batch *out);
 
+/* Give the problems of an existing ensemble new rotational degree counts
+ * n[count] and relaxation times tau[count] (host arrays), keeping their
+ * lengths, buffers and cached launch graphs; a solver pool can so serve
+ * changing sets of problems of one length.  The state is invalidated:
+ * lbm_batch_set_macro must follow before lbm_batch_run. */
+int lbm_batch_set_problems(lbm_batch b, const int *n, const double *tau);
+
 /* Bytes for each state buffer and for the work buffer; total node count. */
 int lbm_batch_sizes(lbm_batch b, size_t *state_bytes, size_t *work_bytes, int64_t *total_nodes);
 
@@ -281,7 +288,8 @@ void lbm_batch_destroy(lbm_batch b);
  * multiple of 128, gradients of the residual stream float32 in the same
  * layout, conv weights bfloat16 [k][C][C].  `impl` selects the tensor-core
  * kernels (0: tcgen05 MMA fed by the Tensor Memory Accelerator, operands
- * 16-byte aligned) or the CUDA-core ones (1).  `status` (device int, may be
+ * 16-byte aligned, persistent blocks; 2: the same, one output tile per
+ * block) or the CUDA-core ones (1).  `status` (device int, may be
  * NULL) receives bit 4 if a tensor-core kernel gave up waiting on a
  * barrier, in which case its outputs are not written.  Calls are
  * asynchronous on `stream`; they return LBM_OK, LBM_EINVAL (bad pointer,
@@ -319,17 +327,20 @@ int lbm_nn_lift(const float *feat, const float *Wl, const float *bl, void *x0, i
                 int C, void *stream);
 
 /* Lift backward, accumulated: gWl[c][j] += sum_p gx0[p][c] feat[p][j],
- * gbl[c] += sum_p gx0[p][c].  C a multiple of 32, at most 1024. */
+ * gbl[c] += sum_p gx0[p][c].  C a multiple of 32, at most 1024; F one of
+ * 4, 8, 16, 32 (patches of 1, 2, 4, 8 nodes). */
 int lbm_nn_lift_backward(const float *gx0, const float *feat, float *gWl, float *gbl, int64_t P,
                          int F, int C, void *stream);
 
-/* Head: out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o], Fo <= 16 float outputs. */
+/* Head: out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o], Fo <= 16 float outputs,
+ * C a multiple of 32, at most 256. */
 int lbm_nn_head(const void *x, const float *Wp, const float *bp, float *out, int64_t P, int C, int Fo,
                 void *stream);
 
 /* Head backward: gx = gout Wp (written), gz = bf16(gx * gelu'(z)) (written;
  * z is the pre-activation of the last conv layer), gWp += gout^T x,
- * gbp += sum_p gout.  C a multiple of 32, at most 256. */
+ * gbp += sum_p gout.  C is 128 or 256; Fo is 3, 6 or 12 (patches of 1, 2,
+ * 4 nodes). */
 int lbm_nn_head_backward(const float *gout, const void *x, const float *Wp, const void *z, float *gx,
                          void *gz, float *gWp, float *gbp, int64_t P, int C, int Fo, void *stream);
 
@@ -341,6 +352,26 @@ int lbm_nn_bias_grad(const void *gz, float *gb, int64_t P, int C, void *stream);
  * place; p -= lr m_hat / (sqrt(v_hat) + eps). */
 int lbm_nn_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
                 float eps, int t, float weight_decay, void *stream);
+
+/* The Adam step with its per-step constants on the device, for training
+ * steps captured in a CUDA graph: t = ++*step (device int64, the count of
+ * completed steps), lr = lr_table[min(t, table_len) - 1] (device float
+ * schedule), bias corrections 1/(1 - b1^t), 1/(1 - b2^t) written to hyper
+ * (device float[3], scratch), then the update of lbm_nn_adam. */
+int lbm_nn_adam_scheduled(float *p, const float *g, float *m, float *v, int64_t n,
+                          const float *lr_table, int64_t table_len, int64_t *step, float *hyper,
+                          float b1, float b2, float eps, float weight_decay, void *stream);
+
+/* Training minibatch drawn on the device from the counter-based generator
+ * SplitMix64: pair i takes h = splitmix64(seed ^ splitmix64(*step * batch +
+ * i)), tube = good[(h & 0xffffffff) mod ngood], window j = (h >> 32) mod
+ * windows, and writes rows_src[i] = j*tubes + tube, rows_dst[i] =
+ * (j+1)*tubes + tube (rows of trajectory fields stored [windows+1][tubes][L])
+ * and gamma_out[i] = gamma_tubes[tube].  good: device int[ngood] indices of
+ * the usable tubes. */
+int lbm_nn_sample_pairs(const int *good, int ngood, int windows, int tubes,
+                        const float *gamma_tubes, uint64_t seed, const int64_t *step, int batch,
+                        int64_t *rows_src, int64_t *rows_dst, float *gamma_out, void *stream);
 
 /* Mean squared error: *loss += mean((out - target)^2) (device double, the
  * caller zeroes it); gout (may be NULL) = 2 (out - target) / n. */
@@ -369,10 +400,16 @@ int lbm_nn_apply(const float *rho, const float *u, const float *T, const float *
  *     rho ((1+n)/2 T + u^2/2), half_dof[b] = (1+n)/2;
  *   l1[b] (may be NULL) = max over rho, u, T of sum|first - second| over
  *     the window divided by sum|rho2|, sum sqrt(gamma T2) and sum|T2|
- *     (the second state is the reference). */
+ *     (the second state is the reference);
+ *   starts (may be NULL; device int[2B]) = a spot-check window of `span`
+ *     nodes centred on the node where |rho2 - rho| is largest (the first one
+ *     on ties; a non-finite change counts as largest):
+ *     starts[b] = clamp(argmax - span/2, 0, L - span), starts[B + b] =
+ *     starts[b] + margin (0 <= 2 margin <= span <= L). */
 int lbm_nn_tube_checks(const float *rho, const float *u, const float *T, const float *rho2,
                        const float *u2, const float *T2, const float *half_dof, const float *gamma,
-                       float *residual, float *l1, int B, int L, int w0, int W, void *stream);
+                       float *residual, float *l1, int *starts, int span, int margin, int B, int L,
+                       int w0, int W, void *stream);
 
 /* Row gather of three float fields stored as rows of row_len nodes:
  * d_f[i*W + w] = f[rows[i]*row_len + offsets[i] + w] for i < count, w < W

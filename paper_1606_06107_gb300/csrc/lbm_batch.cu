@@ -345,6 +345,33 @@ int lbm_batch_create(int count, const int64_t *lengths, const int *n, const doub
     return LBM_OK;
 }
 
+int lbm_batch_set_problems(lbm_batch b, const int *n, const double *tau)
+{
+    if (!b) return LBM_EINVAL;
+    if (!n || !tau) return bfail(b, LBM_EINVAL, "null n or tau");
+    for (int k = 0; k < b->count; ++k)
+        if (n[k] < 0 || !(tau[k] > 0.0) || !std::isfinite(tau[k]))
+            return bfail(b, LBM_EINVAL, "bad n or tau");
+    const double m = b->m_fd;
+    for (int k = 0; k < b->count; ++k) {
+        TubeDesc &d = b->tubes[k];
+        const float om = (float)(1.0 / (m * tau[k]));
+        const float keep = (float)(1.0 - (double)om);
+        d.omega = (float)(1.0 - (double)keep);
+        d.cT = (float)(0.5 * (1 + n[k]));
+        d.half_n = (float)(0.5 * n[k]);
+        d.half_n_r2 = (float)(0.5 * n[k] * b->r * b->r);
+    }
+    if (b->bound) {
+        cudaError_t e = cudaMemcpyAsync(b->work + b->off_tubes, b->tubes.data(),
+                                        sizeof(TubeDesc) * b->count, cudaMemcpyHostToDevice,
+                                        b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "table upload");
+        b->has_state = false;
+    }
+    return LBM_OK;
+}
+
 int lbm_batch_sizes(lbm_batch b, size_t *state_bytes, size_t *work_bytes, int64_t *total_nodes)
 {
     if (!b) return LBM_EINVAL;

@@ -20,8 +20,10 @@
 //   forward       D[pos][co] = sum_{t,ci} x[pos+s_t][ci] W[t][co][ci]   (A, B K-major)
 //   input grad    D[pos][ci] = sum_{t,co} gz[pos+s_t][co] WT[t][ci][co] (A, B K-major)
 //   weight grad   D[co][ci]  = sum_pos gz[pos][co] x[pos+s_t][ci]       (A, B MN-major)
-// A CUDA-core implementation of the same three products (impl = 1) is kept
-// as the comparison point for the tensor-core one.
+// The forward and input-gradient products run persistent (impl 0: one block
+// per SM, double-buffered accumulators so that the epilogue of a tile
+// overlaps the MMAs of the next) or one tile per block (impl 2); a
+// CUDA-core implementation of all three (impl 1) is the comparison point.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -47,17 +49,27 @@ constexpr long long kWaitCycles = 1ll << 32;  // bound on every mbarrier wait (~
 constexpr int kTimeoutBit = 4;      // status bit set when a wait gives up
 
 // ------------------------------------------------------------ math helpers
+// tanh on the special-function unit (tanh.approx.f32: relative error about
+// 2^-11, below the bfloat16 rounding the activations get next)
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// GELU in its tanh form and its derivative.
 __device__ __forceinline__ float gelu(float x)
 {
     const float c = 0.7978845608028654f;  // sqrt(2/pi)
-    const float th = tanhf(c * fmaf(0.044715f * x, x * x, x));
+    const float th = tanh_fast(c * fmaf(0.044715f * x, x * x, x));
     return 0.5f * x * (1.0f + th);
 }
 
 __device__ __forceinline__ float gelu_grad(float x)
 {
     const float c = 0.7978845608028654f;
-    const float th = tanhf(c * fmaf(0.044715f * x, x * x, x));
+    const float th = tanh_fast(c * fmaf(0.044715f * x, x * x, x));
     return 0.5f * (1.0f + th) + 0.5f * x * (1.0f - th * th) * c * fmaf(3.0f * 0.044715f * x, x, 1.0f);
 }
 
@@ -218,6 +230,49 @@ struct ConvArgs {
     int *status;
 };
 
+// Epilogue of 32 consecutive accumulator columns c..c+31 of one position
+// (element offset `base` of column 0 of the tile, output channel n0 + c).
+template <int EPI>
+__device__ __forceinline__ void epilogue32(const ConvArgs &a, const float (&v)[32], int64_t base,
+                                           int n0, int c)
+{
+    if constexpr (EPI == kEpiForward) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float xr[8], yv[8], zv[8];
+            unpack8(*reinterpret_cast<const uint4 *>(a.x + base + c + 8 * q), xr);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float zz = v[8 * q + j] + __ldg(a.bias + n0 + c + 8 * q + j);
+                zv[j] = zz;
+                yv[j] = xr[j] + gelu(zz);
+            }
+            *reinterpret_cast<uint4 *>(a.y + base + c + 8 * q) = pack8(yv);
+            if (a.z) *reinterpret_cast<uint4 *>(a.z + base + c + 8 * q) = pack8(zv);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float g[8];
+            float4 *gp = reinterpret_cast<float4 *>(a.gx + base + c + 8 * q);
+            const float4 g0 = gp[0], g1 = gp[1];
+            g[0] = g0.x + v[8 * q + 0]; g[1] = g0.y + v[8 * q + 1];
+            g[2] = g0.z + v[8 * q + 2]; g[3] = g0.w + v[8 * q + 3];
+            g[4] = g1.x + v[8 * q + 4]; g[5] = g1.y + v[8 * q + 5];
+            g[6] = g1.z + v[8 * q + 6]; g[7] = g1.w + v[8 * q + 7];
+            gp[0] = make_float4(g[0], g[1], g[2], g[3]);
+            gp[1] = make_float4(g[4], g[5], g[6], g[7]);
+            if (a.gzprev) {
+                float zp[8], gz[8];
+                unpack8(*reinterpret_cast<const uint4 *>(a.zprev + base + c + 8 * q), zp);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) gz[j] = g[j] * gelu_grad(zp[j]);
+                *reinterpret_cast<uint4 *>(a.gzprev + base + c + 8 * q) = pack8(gz);
+            }
+        }
+    }
+}
+
 struct Smem {
     uint8_t *tiles;
     uint64_t *full, *empty, *done;
@@ -342,43 +397,243 @@ __global__ void __launch_bounds__(128, 1)
         __syncwarp();  // tcgen05.ld is warp-collective
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
         if (!ok || failed) continue;
-        if constexpr (EPI == kEpiForward) {
+        epilogue32<EPI>(a, v, base, n0, c);
+    }
+    teardown(tmem);
+}
+
+// Persistent form of the forward / input-gradient product: one block per
+// SM walks the output tiles (128 positions x 128 channels) with a stride of
+// the grid.  Warp 0 issues the TMA loads into a 4-stage ring, warp 1 issues
+// the MMAs into one of two 128-column accumulators in tensor memory, and 8
+// epilogue warps drain the other accumulator (warps 2..9: lane quarter
+// warp % 4, columns 0-63 for warps 2-5 and 64-127 for warps 6-9), so the
+// epilogue of one tile overlaps the MMAs of the next.
+constexpr int kPStages = 4;
+constexpr int kEpiWarps = 8;
+constexpr int kPThreads = 64 + 32 * kEpiWarps;
+constexpr int kStagePitch = 68;  // floats per staged row (64 + 4: conflict-free float4 rows)
+constexpr int kStagingBytes = kEpiWarps * 32 * kStagePitch * 4;
+constexpr int kPSmemBytes = kPStages * kStageBytes + kStagingBytes + 1024 + 256;
+
+// Epilogue of one warp's 32 rows x 64 columns of a persistent tile.  The
+// accumulator rows (one per lane after tcgen05.ld) are transposed through a
+// padded shared-memory block so that every global load and store is done
+// cooperatively: half a warp covers the 64 columns of one row, so each
+// instruction touches two whole row segments.
+template <int EPI>
+__device__ __forceinline__ void epilogue_rows(const ConvArgs &a, float *st, uint32_t taddr, int b,
+                                              int l_first, int n0, bool skip)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int c = 0; c < 64; c += 32) {
+        float v[32];
+        __syncwarp();
+        tmem_ld32(taddr + c, v);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float xr[8], yv[8], zv[8];
-                unpack8(*reinterpret_cast<const uint4 *>(a.x + base + c + 8 * q), xr);
+        for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<float4 *>(st + lane * kStagePitch + c + 4 * j) =
+                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
+    __syncwarp();
+    if (!skip) {
+        const int cg = (lane & 15) * 4;
+        float4 bias = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (EPI == kEpiForward) bias = *reinterpret_cast<const float4 *>(a.bias + n0 + cg);
+        // 16 rows per lane (r = lane/16 + 2i) in two groups of 8: all loads of
+        // a group are issued before any result is formed
+#pragma unroll 1
+        for (int r0 = lane >> 4; r0 < 32; r0 += 16) {
+            float4 acc[8], gin[8];
+            uint2 in[8];
+            int64_t off[8];
+            bool live[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float zz = v[8 * q + j] + __ldg(a.bias + n0 + c + 8 * q + j);
-                    zv[j] = zz;
-                    yv[j] = xr[j] + gelu(zz);
+            for (int i = 0; i < 8; ++i) {
+                const int r = r0 + 2 * i, l = l_first + r;
+                live[i] = l < a.L;
+                off[i] = ((int64_t)b * a.L + l) * a.C + n0 + cg;
+                acc[i] = *reinterpret_cast<const float4 *>(st + r * kStagePitch + cg);
+                if (live[i]) {
+                    if constexpr (EPI == kEpiForward) {
+                        in[i] = *reinterpret_cast<const uint2 *>(a.x + off[i]);
+                    } else {
+                        gin[i] = *reinterpret_cast<const float4 *>(a.gx + off[i]);
+                        if (a.gzprev) in[i] = *reinterpret_cast<const uint2 *>(a.zprev + off[i]);
+                    }
                 }
-                *reinterpret_cast<uint4 *>(a.y + base + c + 8 * q) = pack8(yv);
-                if (a.z) *reinterpret_cast<uint4 *>(a.z + base + c + 8 * q) = pack8(zv);
             }
-        } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float g[8];
-                float4 *gp = reinterpret_cast<float4 *>(a.gx + base + c + 8 * q);
-                const float4 g0 = gp[0], g1 = gp[1];
-                g[0] = g0.x + v[8 * q + 0]; g[1] = g0.y + v[8 * q + 1];
-                g[2] = g0.z + v[8 * q + 2]; g[3] = g0.w + v[8 * q + 3];
-                g[4] = g1.x + v[8 * q + 4]; g[5] = g1.y + v[8 * q + 5];
-                g[6] = g1.z + v[8 * q + 6]; g[7] = g1.w + v[8 * q + 7];
-                gp[0] = make_float4(g[0], g[1], g[2], g[3]);
-                gp[1] = make_float4(g[4], g[5], g[6], g[7]);
-                if (a.gzprev) {
-                    float zp[8], gz[8];
-                    unpack8(*reinterpret_cast<const uint4 *>(a.zprev + base + c + 8 * q), zp);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) gz[j] = g[j] * gelu_grad(zp[j]);
-                    *reinterpret_cast<uint4 *>(a.gzprev + base + c + 8 * q) = pack8(gz);
+            for (int i = 0; i < 8; ++i) {
+                if (!live[i]) continue;
+                const int64_t o = off[i];
+                if constexpr (EPI == kEpiForward) {
+                    const float2 x01 =
+                        __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&in[i].x));
+                    const float2 x23 =
+                        __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&in[i].y));
+                    const float z0 = acc[i].x + bias.x, z1 = acc[i].y + bias.y,
+                                z2 = acc[i].z + bias.z, z3 = acc[i].w + bias.w;
+                    uint2 yv;
+                    *reinterpret_cast<__nv_bfloat162 *>(&yv.x) =
+                        __floats2bfloat162_rn(x01.x + gelu(z0), x01.y + gelu(z1));
+                    *reinterpret_cast<__nv_bfloat162 *>(&yv.y) =
+                        __floats2bfloat162_rn(x23.x + gelu(z2), x23.y + gelu(z3));
+                    *reinterpret_cast<uint2 *>(a.y + o) = yv;
+                    if (a.z) {
+                        uint2 zv;
+                        *reinterpret_cast<__nv_bfloat162 *>(&zv.x) = __floats2bfloat162_rn(z0, z1);
+                        *reinterpret_cast<__nv_bfloat162 *>(&zv.y) = __floats2bfloat162_rn(z2, z3);
+                        *reinterpret_cast<uint2 *>(a.z + o) = zv;
+                    }
+                } else {
+                    float4 g = gin[i];
+                    g.x += acc[i].x, g.y += acc[i].y, g.z += acc[i].z, g.w += acc[i].w;
+                    *reinterpret_cast<float4 *>(a.gx + o) = g;
+                    if (a.gzprev) {
+                        const float2 z01 =
+                            __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&in[i].x));
+                        const float2 z23 =
+                            __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&in[i].y));
+                        uint2 gv;
+                        *reinterpret_cast<__nv_bfloat162 *>(&gv.x) =
+                            __floats2bfloat162_rn(g.x * gelu_grad(z01.x), g.y * gelu_grad(z01.y));
+                        *reinterpret_cast<__nv_bfloat162 *>(&gv.y) =
+                            __floats2bfloat162_rn(g.z * gelu_grad(z23.x), g.w * gelu_grad(z23.y));
+                        *reinterpret_cast<uint2 *>(a.gzprev + o) = gv;
+                    }
                 }
             }
         }
     }
-    teardown(tmem);
+    __syncwarp();  // the staging block is rewritten by the next tile
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kPThreads, 1)
+    k_conv_tcp(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
+               ConvArgs a, int tiles_l, int tiles_n, int total)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *tiles = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    float *staging = (float *)(tiles + kPStages * kStageBytes);
+    uint64_t *full = (uint64_t *)(tiles + kPStages * kStageBytes + kStagingBytes);
+    uint64_t *empty = full + kPStages;
+    uint64_t *tfull = empty + kPStages;   // accumulator a ready for the epilogue
+    uint64_t *tempty = tfull + 2;         // accumulator a drained by the epilogue
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
+    __shared__ volatile int failed;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kPStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], kEpiWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
+    __syncwarp();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(saddr(tmem_slot)), "r"(2 * kTile) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int chunks = a.C / kChunk, nk = a.k * chunks;
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            int g = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+                const int n0 = (tile % tiles_n) * kTile, rest = tile / tiles_n;
+                const int b = rest / tiles_l, l0 = (rest % tiles_l) * kTile;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int st = g % kPStages, use = g / kPStages;
+                    if (use > 0 && !mbar_wait(&empty[st], (use - 1) & 1, a.status)) {
+                        failed = 1;
+                        ok = false;
+                        break;
+                    }
+                    const int t = kb / chunks, c0 = (kb % chunks) * kChunk;
+                    uint8_t *buf = tiles + st * kStageBytes;
+                    mbar_expect_tx(&full[st], kStageBytes);
+                    tma_load_3d(buf, &map_a, &full[st], c0, l0 + (t - a.k / 2) * a.dil, b);
+                    tma_load_2d(buf + kStageBytes / 2, &map_w, &full[st], c0, t * a.C + n0);
+                }
+            }
+            // wait (bounded) for the last loads so that none lands after exit
+            for (int q = std::max(0, g - kPStages); q < g; ++q)
+                mbar_wait(&full[q % kPStages], (q / kPStages) & 1, a.status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            constexpr uint32_t idesc = instr_desc(0, 0);
+            int g = 0, it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x, ++it) {
+                const int acc = it & 1, use = it >> 1;
+                const uint32_t d = tmem + acc * kTile;
+                if (use > 0 && !mbar_wait(&tempty[acc], (use - 1) & 1, a.status)) {
+                    failed = 1;
+                    break;
+                }
+                tc_fence_after();
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int st = g % kPStages;
+                    if (!mbar_wait(&full[st], (g / kPStages) & 1, a.status)) {
+                        failed = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t at = saddr(tiles + st * kStageBytes);
+                    const uint32_t bt = at + kStageBytes / 2;
+#pragma unroll
+                    for (int kk = 0; kk < kChunk / 16; ++kk)
+                        mma_bf16(d, smem_desc(at + kk * 32, 16, 1024),
+                                 smem_desc(bt + kk * 32, 16, 1024), idesc, (kb | kk) != 0);
+                    mma_commit(&empty[st]);
+                }
+                mma_commit(&tfull[acc]);
+            }
+        }
+    } else {  // epilogue warps
+        const int e = warp - 2, quarter = warp & 3, col0 = (e >> 2) * 64;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
+            const int acc = it & 1, use = it >> 1;
+            const int n0 = (tile % tiles_n) * kTile, rest = tile / tiles_n;
+            const int b = rest / tiles_l, l0 = (rest % tiles_l) * kTile;
+            bool ready = mbar_wait(&tfull[acc], use & 1, a.status);
+            __syncwarp();
+            if (!ready) failed = 1;
+            tc_fence_after();
+            epilogue_rows<EPI>(a, staging + e * 32 * kStagePitch,
+                               tmem + acc * kTile + ((uint32_t)(quarter * 32) << 16) + col0, b,
+                               l0 + quarter * 32, n0 + col0, failed != 0);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&tempty[acc]))
+                                        : "memory");
+            if (failed) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTile)
+                     : "memory");
+    }
 }
 
 // Weight gradient: one block reduces the positions of blocks [q0, q1) (64
@@ -583,97 +838,116 @@ int grid_for(int64_t n, int threads = 256)
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 16));
 }
 
-// x0[p][c] = bf16(sum_j feat[p][j] Wl[c][j] + bl[c]); F <= 64 features
+// x0[p][c] = bf16(sum_j feat[p][j] Wl[c][j] + bl[c]); F <= 64 features.  The
+// weights sit transposed in shared memory (wsh[j][c]) so that the threads of
+// a warp, which take consecutive channels, read consecutive banks.
 __global__ void k_lift(const float *feat, const float *Wl, const float *bl, __nv_bfloat16 *x0,
                        int64_t P, int F, int C)
 {
-    extern __shared__ float wsh[];  // [C][F] then [C]
-    for (int i = threadIdx.x; i < C * F; i += blockDim.x) wsh[i] = Wl[i];
+    extern __shared__ float wsh[];  // [F][C] then [C]
+    for (int i = threadIdx.x; i < C * F; i += blockDim.x) wsh[(i % F) * C + i / F] = Wl[i];
     for (int i = threadIdx.x; i < C; i += blockDim.x) wsh[C * F + i] = bl[i];
     __syncthreads();
     const int64_t n = P * C;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = i / C;
-        const int c = (int)(i % C);
+        const int c = (int)(i - p * C);
+        const float *f = feat + p * F;
         float s = wsh[C * F + c];
-        for (int j = 0; j < F; ++j) s = fmaf(feat[p * F + j], wsh[c * F + j], s);
+        for (int j = 0; j < F; ++j) s = fmaf(__ldg(f + j), wsh[j * C + c], s);
         x0[i] = __float2bfloat16_rn(s);
     }
 }
 
-// out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o]: one warp per position.
+// out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o]: one warp per position, each
+// lane holding channels lane + 32 j (C <= 256), reduced by shuffles.
 __global__ void k_head(const __nv_bfloat16 *x, const float *Wp, const float *bp, float *out,
                        int64_t P, int C, int Fo)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, nj = C / 32;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
+        float xv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xv[j] = j < nj ? __bfloat162float(x[p * C + lane + 32 * j]) : 0.f;
         for (int o = 0; o < Fo; ++o) {
             float s = 0.f;
-            for (int c = lane; c < C; c += 32)
-                s = fmaf(__bfloat162float(x[p * C + c]), __ldg(Wp + o * C + c), s);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < nj) s = fmaf(xv[j], __ldg(Wp + o * C + lane + 32 * j), s);
             for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == 0) out[p * Fo + o] = s + bp[o];
+            if (lane == o) out[p * Fo + o] = s + bp[o];
         }
     }
 }
 
 // Head backward: gx = gout Wp; gz = bf16(gx gelu'(z)); gWp += gout^T x; gbp += sum gout.
-// One warp per position, lanes over channels (C <= 256, Fo <= 16).
+// One warp per position, lane holding channels lane + 32 j (NJ = C / 32),
+// FO outputs: both compile-time so that the partial sums stay in registers.
+template <int NJ, int FO>
 __global__ void k_head_bwd(const float *gout, const __nv_bfloat16 *x, const float *Wp,
                            const __nv_bfloat16 *z, float *gx, __nv_bfloat16 *gz, float *gWp,
-                           float *gbp, int64_t P, int C, int Fo)
+                           float *gbp, int64_t P)
 {
+    constexpr int C = 32 * NJ;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    constexpr int kMaxFo = 16, kMaxCL = 8;
-    float accW[kMaxFo][kMaxCL];
-    float accB[kMaxFo];
-    for (int o = 0; o < kMaxFo; ++o) {
+    float accW[FO][NJ], accB[FO], wp[FO][NJ];
+#pragma unroll
+    for (int o = 0; o < FO; ++o) {
         accB[o] = 0.f;
-        for (int j = 0; j < kMaxCL; ++j) accW[o][j] = 0.f;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) accW[o][j] = 0.f, wp[o][j] = __ldg(Wp + o * C + lane + 32 * j);
     }
     for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
-        float go[kMaxFo];
-        for (int o = 0; o < Fo; ++o) {
-            go[o] = gout[p * Fo + o];
+        float go[FO];
+#pragma unroll
+        for (int o = 0; o < FO; ++o) {
+            go[o] = __ldg(gout + p * FO + o);
             accB[o] += go[o];
         }
-        for (int j = 0; j < C / 32; ++j) {
-            const int c = lane + 32 * j;
-            const float xv = __bfloat162float(x[p * C + c]);
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int64_t c = p * C + lane + 32 * j;
+            const float xv = __bfloat162float(x[c]);
             float g = 0.f;
-            for (int o = 0; o < Fo; ++o) {
-                g = fmaf(go[o], __ldg(Wp + o * C + c), g);
+#pragma unroll
+            for (int o = 0; o < FO; ++o) {
+                g = fmaf(go[o], wp[o][j], g);
                 accW[o][j] = fmaf(go[o], xv, accW[o][j]);
             }
-            gx[p * C + c] = g;
-            gz[p * C + c] = __float2bfloat16_rn(g * gelu_grad(__bfloat162float(z[p * C + c])));
+            gx[c] = g;
+            gz[c] = __float2bfloat16_rn(g * gelu_grad(__bfloat162float(z[c])));
         }
     }
-    for (int o = 0; o < Fo; ++o) {
-        for (int j = 0; j < C / 32; ++j) atomicAdd(&gWp[o * C + lane + 32 * j], accW[o][j]);
+#pragma unroll
+    for (int o = 0; o < FO; ++o) {
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) atomicAdd(&gWp[o * C + lane + 32 * j], accW[o][j]);
         if (lane == 0) atomicAdd(&gbp[o], accB[o]);
     }
 }
 
 // Lift backward: gWl[c][j] += sum_p gx0[p][c] feat[p][j]; gbl[c] += sum_p gx0[p][c].
-// Threads over channels, blocks over position ranges.
+// Threads over channels, blocks over position ranges, F features compile-time.
+template <int F>
 __global__ void k_lift_bwd(const float *gx0, const float *feat, float *gWl, float *gbl, int64_t P,
-                           int F, int C, int64_t per_block)
+                           int C, int64_t per_block)
 {
     const int c = threadIdx.x;  // blockDim.x == C
-    constexpr int kMaxF = 64;
-    float acc[kMaxF];
-    for (int j = 0; j < kMaxF; ++j) acc[j] = 0.f;
+    float acc[F];
+#pragma unroll
+    for (int j = 0; j < F; ++j) acc[j] = 0.f;
     float accb = 0.f;
     const int64_t p0 = blockIdx.x * per_block, p1 = std::min(P, p0 + per_block);
     for (int64_t p = p0; p < p1; ++p) {
         const float g = gx0[p * C + c];
         accb += g;
+#pragma unroll
         for (int j = 0; j < F; ++j) acc[j] = fmaf(g, __ldg(feat + p * F + j), acc[j]);
     }
+#pragma unroll
     for (int j = 0; j < F; ++j) atomicAdd(&gWl[c * F + j], acc[j]);
     atomicAdd(&gbl[c], accb);
 }
@@ -716,6 +990,61 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, int64_t n, 
         v[i] = vi;
         p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
     }
+}
+
+// Adam's per-step constants from a device step counter, so that a captured
+// training step replays with the right learning rate and bias corrections:
+// t = ++*step; hyper = (lr_table[min(t, len) - 1], 1 / (1 - b1^t), 1 / (1 - b2^t)).
+__global__ void k_adam_prep(int64_t *step, const float *lr_table, int64_t len, float b1, float b2,
+                            float *hyper)
+{
+    const int64_t t = ++*step;
+    hyper[0] = lr_table[(t < len ? t : len) - 1];
+    hyper[1] = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+    hyper[2] = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
+}
+
+__global__ void k_adam_dev(float *p, const float *g, float *m, float *v, int64_t n,
+                           const float *hyper, float b1, float b2, float eps, float wd)
+{
+    const float lr = hyper[0], c1 = hyper[1], c2 = hyper[2];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i] + wd * p[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+// SplitMix64 (Steele, Lea and Flood, 2014): a counter-based generator, here
+// keyed by (seed, step, i).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Minibatch of training pairs drawn on the device: pair i of the step
+// *step takes tube good[h mod ngood] and window j = (h >> 32) mod windows,
+// h = splitmix64(seed ^ splitmix64(step * batch + i)); rows index the
+// trajectory fields stored window-major ([windows + 1][tubes][L]).
+__global__ void k_sample_pairs(const int *good, int ngood, int windows, int tubes,
+                               const float *gamma_tubes, uint64_t seed, const int64_t *step,
+                               int batch, int64_t *rows_src, int64_t *rows_dst, float *gamma_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= batch) return;
+    const uint64_t h = splitmix64(seed ^ splitmix64((uint64_t)(*step) * (uint64_t)batch + i));
+    const int tube = good[(int)((h & 0xFFFFFFFFull) % (uint64_t)ngood)];
+    const int j = (int)((h >> 32) % (uint64_t)windows);
+    rows_src[i] = (int64_t)j * tubes + tube;
+    rows_dst[i] = (int64_t)(j + 1) * tubes + tube;
+    gamma_out[i] = gamma_tubes[tube];
 }
 
 // loss partial sums (double) and gout = 2 (out - target) / n
@@ -792,15 +1121,23 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 // One block per tube: conservation residual between two states (mass,
 // momentum scaled by mass, total energy with (1+n)/2 T) and, when a
 // reference is given, the L1 error (max over rho, u relative to the sound
-// speed, T).  Window [w0, w0 + W) of each tube of length L.
+// speed, T).  Window [w0, w0 + W) of each tube of length L.  With `starts`,
+// also the spot-check window of `span` nodes centred on the node where rho
+// changes most: starts[b] = clamp(argmax - span/2, 0, L - span) and
+// starts[B + b] = starts[b] + margin.
 __global__ void k_tube_checks(const float *rho, const float *u, const float *T, const float *rho2,
                               const float *u2, const float *T2, const float *half_dof,
-                              const float *gamma, float *residual, float *l1, int L, int w0, int W)
+                              const float *gamma, float *residual, float *l1, int *starts, int L,
+                              int w0, int W, int span, int margin)
 {
     __shared__ double red[32];
+    __shared__ float best_v[32];
+    __shared__ int best_i[32];
     const int b = blockIdx.x;
     const double cv = half_dof ? (double)half_dof[b] : 0.0;  // only read when residual is asked for
     double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    float bv = -1.0f;
+    int bi = w0;
     for (int l = w0 + threadIdx.x; l < w0 + W; l += blockDim.x) {
         const int64_t i = (int64_t)b * L + l;
         const double r1 = rho[i], v1 = u[i], t1 = T[i], r2 = rho2[i], v2 = u2[i], t2 = T2[i];
@@ -813,6 +1150,11 @@ __global__ void k_tube_checks(const float *rho, const float *u, const float *T, 
         s[6] += fabs(r1 - r2);
         s[7] += fabs(v1 - v2);
         s[8] += fabs(t1 - t2);
+        const float d = fabsf(rho2[i] - rho[i]);
+        if (!(d <= bv)) {  // also takes a non-finite change
+            bv = isfinite(d) ? d : INFINITY;
+            bi = l;
+        }
     }
     double tot[9];
     for (int q = 0; q < 9; ++q) tot[q] = block_sum(s[q], red);
@@ -827,6 +1169,22 @@ __global__ void k_tube_checks(const float *rho, const float *u, const float *T, 
         }
         cs = block_sum(cs, red);
         ts = block_sum(ts, red);
+    }
+    if (starts) {  // argmax of |rho2 - rho|, smallest index on ties
+        for (int off = 16; off > 0; off >>= 1) {
+            const float ov = __shfl_down_sync(0xffffffffu, bv, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+            if (ov > bv || (ov == bv && oi < bi)) bv = ov, bi = oi;
+        }
+        if ((threadIdx.x & 31) == 0) best_v[threadIdx.x >> 5] = bv, best_i[threadIdx.x >> 5] = bi;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                if (best_v[w] > bv || (best_v[w] == bv && best_i[w] < bi)) bv = best_v[w], bi = best_i[w];
+            const int st = min(max(bi - span / 2, 0), L - span);
+            starts[b] = st;
+            starts[gridDim.x + b] = st + margin;
+        }
     }
     if (threadIdx.x == 0) {
         if (residual) {
@@ -928,7 +1286,11 @@ int set_smem_attrs()
         cudaFuncSetAttribute(k_conv_tc<kEpiInputGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSmemBytes) != cudaSuccess ||
         cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
-            cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_tcp<kEpiForward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kPSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_tcp<kEpiInputGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kPSmemBytes) != cudaSuccess)
         return LBM_ECUDA;
     done[dev] = true;
     return LBM_OK;
@@ -942,7 +1304,25 @@ bool conv_shape_ok(int B, int L, int C, int k, int dil, int impl)
         return false;
     if ((int64_t)(k / 2) * dil >= (1 << 20) || (int64_t)B * L * C >= (1ll << 40)) return false;
     if (impl == 1) return k <= kSimtMaxK && (k - 1) * dil <= kSimtMaxSpan - kSimtTX;
-    return impl == 0 && (int64_t)k * C <= (1 << 20);
+    return (impl == 0 || impl == 2) && (int64_t)k * C <= (1 << 20);
+}
+
+// SM count of the current device, looked up once per device (so that calls
+// made while a stream is being captured into a graph query nothing)
+int sm_count()
+{
+    static std::mutex mu;
+    static int count[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (count[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            return 0;
+        count[dev] = n;
+    }
+    return count[dev];
 }
 
 int conv_common(int epi, const void *in, const void *w, const ConvArgs &a, int impl, void *stream)
@@ -963,11 +1343,25 @@ int conv_common(int epi, const void *in, const void *w, const ConvArgs &a, int i
     if (rc != LBM_OK) return rc;
     CUtensorMap ma, mw;
     if (!map_act(&ma, in, a.B, a.L, a.C, kTile) || !map_w(&mw, w, a.C, a.k)) return LBM_ECUDA;
-    const dim3 grid((a.L + kTile - 1) / kTile, a.C / kTile, a.B);
+    const int tiles_l = (a.L + kTile - 1) / kTile, tiles_n = a.C / kTile;
+    if (impl == 2) {  // one output tile per block
+        const dim3 grid(tiles_l, tiles_n, a.B);
+        if (epi == kEpiForward)
+            k_conv_tc<kEpiForward><<<grid, 128, kSmemBytes, s>>>(ma, mw, a);
+        else
+            k_conv_tc<kEpiInputGrad><<<grid, 128, kSmemBytes, s>>>(ma, mw, a);
+        return launched(cudaGetLastError());
+    }
+    const int64_t total = (int64_t)tiles_l * tiles_n * a.B;
+    const int sms = sm_count();
+    if (sms < 1 || total >= (1ll << 31)) return LBM_ECUDA;
+    const int grid = (int)std::min<int64_t>(total, sms);
     if (epi == kEpiForward)
-        k_conv_tc<kEpiForward><<<grid, 128, kSmemBytes, s>>>(ma, mw, a);
+        k_conv_tcp<kEpiForward><<<grid, kPThreads, kPSmemBytes, s>>>(ma, mw, a, tiles_l, tiles_n,
+                                                                      (int)total);
     else
-        k_conv_tc<kEpiInputGrad><<<grid, 128, kSmemBytes, s>>>(ma, mw, a);
+        k_conv_tcp<kEpiInputGrad><<<grid, kPThreads, kPSmemBytes, s>>>(ma, mw, a, tiles_l, tiles_n,
+                                                                        (int)total);
     return launched(cudaGetLastError());
 }
 
@@ -1058,18 +1452,26 @@ int lbm_nn_lift(const float *feat, const float *Wl, const float *bl, void *x0, i
 int lbm_nn_lift_backward(const float *gx0, const float *feat, float *gWl, float *gbl, int64_t P,
                          int F, int C, void *stream)
 {
-    if (!gx0 || !feat || !gWl || !gbl || P < 1 || F < 1 || F > 64 || C < 32 || C > 1024 || C % 32)
+    if (!gx0 || !feat || !gWl || !gbl || P < 1 || C < 32 || C > 1024 || C % 32 ||
+        (F != 4 && F != 8 && F != 16 && F != 32))
         return LBM_EINVAL;
     const int64_t per_block = std::max<int64_t>(64, (P + 1215) / 1216);
     const int blocks = (int)((P + per_block - 1) / per_block);
-    k_lift_bwd<<<blocks, C, 0, (cudaStream_t)stream>>>(gx0, feat, gWl, gbl, P, F, C, per_block);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (F) {
+    case 4: k_lift_bwd<4><<<blocks, C, 0, s>>>(gx0, feat, gWl, gbl, P, C, per_block); break;
+    case 8: k_lift_bwd<8><<<blocks, C, 0, s>>>(gx0, feat, gWl, gbl, P, C, per_block); break;
+    case 16: k_lift_bwd<16><<<blocks, C, 0, s>>>(gx0, feat, gWl, gbl, P, C, per_block); break;
+    default: k_lift_bwd<32><<<blocks, C, 0, s>>>(gx0, feat, gWl, gbl, P, C, per_block); break;
+    }
     return launched(cudaGetLastError());
 }
 
 int lbm_nn_head(const void *x, const float *Wp, const float *bp, float *out, int64_t P, int C, int Fo,
                 void *stream)
 {
-    if (!x || !Wp || !bp || !out || P < 1 || C < 1 || Fo < 1 || Fo > 16) return LBM_EINVAL;
+    if (!x || !Wp || !bp || !out || P < 1 || C < 32 || C > 256 || C % 32 || Fo < 1 || Fo > 16)
+        return LBM_EINVAL;
     k_head<<<grid_for(P * 32), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)x, Wp, bp, out,
                                                                P, C, Fo);
     return launched(cudaGetLastError());
@@ -1078,12 +1480,26 @@ int lbm_nn_head(const void *x, const float *Wp, const float *bp, float *out, int
 int lbm_nn_head_backward(const float *gout, const void *x, const float *Wp, const void *z, float *gx,
                          void *gz, float *gWp, float *gbp, int64_t P, int C, int Fo, void *stream)
 {
-    if (!gout || !x || !Wp || !z || !gx || !gz || !gWp || !gbp || P < 1 || C < 32 || C > 256 ||
-        C % 32 || Fo < 1 || Fo > 16)
+    if (!gout || !x || !Wp || !z || !gx || !gz || !gWp || !gbp || P < 1 ||
+        (C != 128 && C != 256) || (Fo != 3 && Fo != 6 && Fo != 12))
         return LBM_EINVAL;
-    k_head_bwd<<<std::min<int64_t>(grid_for(P * 32), 152 * 4), 256, 0, (cudaStream_t)stream>>>(
-        gout, (const __nv_bfloat16 *)x, Wp, (const __nv_bfloat16 *)z, gx, (__nv_bfloat16 *)gz, gWp,
-        gbp, P, C, Fo);
+    const int grid = (int)std::min<int64_t>(grid_for(P * 32), 152 * 4);
+    cudaStream_t s = (cudaStream_t)stream;
+    auto xb = (const __nv_bfloat16 *)x;
+    auto zb = (const __nv_bfloat16 *)z;
+    auto gzb = (__nv_bfloat16 *)gz;
+#define LBM_HEAD_BWD(NJ, FO) \
+    k_head_bwd<NJ, FO><<<grid, 256, 0, s>>>(gout, xb, Wp, zb, gx, gzb, gWp, gbp, P)
+    if (C == 128) {
+        if (Fo == 3) LBM_HEAD_BWD(4, 3);
+        else if (Fo == 6) LBM_HEAD_BWD(4, 6);
+        else LBM_HEAD_BWD(4, 12);
+    } else {
+        if (Fo == 3) LBM_HEAD_BWD(8, 3);
+        else if (Fo == 6) LBM_HEAD_BWD(8, 6);
+        else LBM_HEAD_BWD(8, 12);
+    }
+#undef LBM_HEAD_BWD
     return launched(cudaGetLastError());
 }
 
@@ -1105,6 +1521,32 @@ int lbm_nn_adam(float *p, const float *g, float *m, float *v, int64_t n, float l
     const float c2 = (float)(1.0 / (1.0 - std::pow((double)b2, t)));
     k_adam<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2,
                                                           weight_decay);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_adam_scheduled(float *p, const float *g, float *m, float *v, int64_t n,
+                          const float *lr_table, int64_t table_len, int64_t *step, float *hyper,
+                          float b1, float b2, float eps, float weight_decay, void *stream)
+{
+    if (!p || !g || !m || !v || !lr_table || !step || !hyper || n < 1 || table_len < 1)
+        return LBM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_adam_prep<<<1, 1, 0, s>>>(step, lr_table, table_len, b1, b2, hyper);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return LBM_ECUDA;
+    k_adam_dev<<<grid_for(n), 256, 0, s>>>(p, g, m, v, n, hyper, b1, b2, eps, weight_decay);
+    return launched(cudaGetLastError());
+}
+
+int lbm_nn_sample_pairs(const int *good, int ngood, int windows, int tubes,
+                        const float *gamma_tubes, uint64_t seed, const int64_t *step, int batch,
+                        int64_t *rows_src, int64_t *rows_dst, float *gamma_out, void *stream)
+{
+    if (!good || ngood < 1 || windows < 1 || tubes < 1 || !gamma_tubes || !step || batch < 1 ||
+        !rows_src || !rows_dst || !gamma_out)
+        return LBM_EINVAL;
+    k_sample_pairs<<<(batch + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
+        good, ngood, windows, tubes, gamma_tubes, seed, step, batch, rows_src, rows_dst, gamma_out);
     return launched(cudaGetLastError());
 }
 
@@ -1151,13 +1593,15 @@ int lbm_nn_apply(const float *rho, const float *u, const float *T, const float *
 
 int lbm_nn_tube_checks(const float *rho, const float *u, const float *T, const float *rho2,
                        const float *u2, const float *T2, const float *half_dof, const float *gamma,
-                       float *residual, float *l1, int B, int L, int w0, int W, void *stream)
+                       float *residual, float *l1, int *starts, int span, int margin, int B, int L,
+                       int w0, int W, void *stream)
 {
     if (!rho || !u || !T || !rho2 || !u2 || !T2 || B < 1 || L < 1 || w0 < 0 || W < 1 ||
-        w0 + W > L || (!residual && !l1) || (residual && !half_dof) || (l1 && !gamma))
+        w0 + W > L || (!residual && !l1 && !starts) || (residual && !half_dof) || (l1 && !gamma))
         return LBM_EINVAL;
+    if (starts && (span < 1 || span > L || margin < 0 || 2 * margin > span)) return LBM_EINVAL;
     k_tube_checks<<<B, 256, 0, (cudaStream_t)stream>>>(rho, u, T, rho2, u2, T2, half_dof, gamma,
-                                                       residual, l1, L, w0, W);
+                                                       residual, l1, starts, L, w0, W, span, margin);
     return launched(cudaGetLastError());
 }
 

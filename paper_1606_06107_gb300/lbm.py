@@ -56,6 +56,8 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                         ctypes.c_int, ctypes.POINTER(_vp)]),
+    "lbm_batch_set_problems": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_double)]),
     "lbm_batch_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t),
                                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i64)]),
     "lbm_batch_bind": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t,
@@ -91,11 +93,17 @@ SIGNATURES = {
                                    ctypes.c_float, ctypes.c_float, ctypes.c_int,
                                    ctypes.c_float, _vp]),
     "lbm_nn_mse": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp]),
+    "lbm_nn_adam_scheduled": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp,
+                                             ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                             ctypes.c_float, _vp]),
+    "lbm_nn_sample_pairs": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                           ctypes.c_uint64, _vp, ctypes.c_int, _vp, _vp, _vp,
+                                           _vp]),
     "lbm_nn_features": (ctypes.c_int, [_vp] * 5 + [ctypes.c_int, ctypes.c_int,
                                                    ctypes.POINTER(ctypes.c_float), _vp]),
     "lbm_nn_targets": (ctypes.c_int, [_vp] * 7 + [_i64, ctypes.POINTER(ctypes.c_float), _vp]),
     "lbm_nn_apply": (ctypes.c_int, [_vp] * 7 + [_i64, ctypes.POINTER(ctypes.c_float), _vp]),
-    "lbm_nn_tube_checks": (ctypes.c_int, [_vp] * 10 + [ctypes.c_int] * 4 + [_vp]),
+    "lbm_nn_tube_checks": (ctypes.c_int, [_vp] * 11 + [ctypes.c_int] * 6 + [_vp]),
     "lbm_nn_gather": (ctypes.c_int, [_vp] * 5 + [ctypes.c_int, _i64, ctypes.c_int]
                       + [_vp] * 4),
     "lbm_nn_scatter": (ctypes.c_int, [_vp] * 5 + [ctypes.c_int, _i64, ctypes.c_int]
@@ -371,6 +379,16 @@ class LbmBatch:
         with self.torch.cuda.device(self.device):
             self._check(self.lib.lbm_batch_status(self.h, st, ctypes.byref(bad)))
         return np.array(st[:]), bad.value
+
+    def set_problems(self, n, tau):
+        """New rotational degree counts and relaxation times for the same
+        problem lengths (lbm_batch_set_problems); set_macro must follow."""
+        nn = np.ascontiguousarray(np.broadcast_to(n, (self.count,)), dtype=np.int32)
+        tt = np.ascontiguousarray(np.broadcast_to(tau, (self.count,)), dtype=np.float64)
+        with self.torch.cuda.device(self.device):
+            self._check(self.lib.lbm_batch_set_problems(
+                self.h, nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                tt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
     def set_block(self, threads: int, blocks_per_sm: int = 0):
         self._check(self.lib.lbm_batch_set_block(self.h, int(threads), int(blocks_per_sm)))

@@ -368,17 +368,26 @@ def output_scales(tr: Trajectories, sample=64):
 
 class Trainer:
     """Minibatch training of a ConvOperator on restarted-method pairs
-    (state_j -> state_{j+1}) of the tubes the solver kept finite."""
+    (state_j -> state_{j+1}) of the tubes the solver kept finite.
 
-    def __init__(self, net: ConvOperator, tr: Trajectories, batch=32, seed=0):
+    ``step(lr)`` runs one step from the host (minibatch drawn by NumPy).
+    ``run(lrs)`` runs ``len(lrs)`` steps with the learning-rate schedule
+    ``lrs`` as replays of one CUDA graph: the minibatch is drawn on the
+    device (lbm_nn_sample_pairs), the learning rate and Adam's bias
+    corrections come from a device step counter (lbm_nn_adam_scheduled), so
+    a step costs one graph launch."""
+
+    def __init__(self, net: ConvOperator, tr: Trajectories, batch=32, seed=0, max_steps=1 << 20):
         import torch
         self.net, self.tr, self.batch, self.torch = net, tr, batch, torch
+        self.seed = seed
         self.rng = np.random.default_rng(seed)
         self.good = np.flatnonzero(tr.ok)
         if self.good.size == 0:
             raise LbmError(-1, "no finite trajectories to train on")
         dev = net.device
         self.gamma = torch.as_tensor(tr.gamma.astype(np.float32), device=dev)
+        self.good_dev = torch.as_tensor(self.good.astype(np.int32), device=dev)
         self.rows_src = torch.empty(batch, dtype=torch.int64, device=dev)
         self.rows_dst = torch.empty(batch, dtype=torch.int64, device=dev)
         self.gam_b = torch.empty(batch, dtype=torch.float32, device=dev)
@@ -387,6 +396,11 @@ class Trainer:
         self.b = [torch.empty(batch * L, dtype=torch.float32, device=dev) for _ in range(3)]
         self.feat = torch.empty(batch * L * 4, dtype=torch.float32, device=dev)
         self.target = torch.empty(batch * L * 3, dtype=torch.float32, device=dev)
+        self.max_steps = max_steps
+        self.lr_table = torch.zeros(max_steps, dtype=torch.float32, device=dev)
+        self.step_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.hyper = torch.zeros(3, dtype=torch.float32, device=dev)
+        self.graph = None
 
     def sample(self):
         tr, B = self.tr, self.batch
@@ -413,6 +427,62 @@ class Trainer:
         self.net.adam(lr)
         return loss
 
+    # ------------------------------------------------------- graph replays
+    def _device_step(self):
+        net, tr, lib = self.net, self.tr, self.net.lib
+        s = self.torch.cuda.current_stream(net.device).cuda_stream
+        rc = lib.lbm_nn_sample_pairs(_fp(self.good_dev), int(self.good.size), tr.J, tr.B,
+                                     _fp(self.gamma), self.seed, _fp(self.step_dev), self.batch,
+                                     _fp(self.rows_src), _fp(self.rows_dst), _fp(self.gam_b), s)
+        if rc != 0:
+            raise LbmError(rc, "lbm_nn_sample_pairs")
+        self.load(self.rows_src, self.rows_dst)
+        net.loss_and_grad(self.feat, self.target, self.batch, tr.L)
+        rc = lib.lbm_nn_adam_scheduled(_fp(net.params), _fp(net.grads), _fp(net.m), _fp(net.v),
+                                       net.size, _fp(self.lr_table), self.max_steps,
+                                       _fp(self.step_dev), _fp(self.hyper), 0.9, 0.999, 1e-8,
+                                       0.0, s)
+        if rc != 0:
+            raise LbmError(rc, "lbm_nn_adam_scheduled")
+        net._cast()
+
+    def _capture(self):
+        t = self.torch
+        side = t.cuda.Stream(device=self.net.device)
+        side.wait_stream(t.cuda.current_stream(self.net.device))
+        saved = [x.clone() for x in (self.net.params, self.net.m, self.net.v, self.step_dev)]
+        with t.cuda.stream(side):       # one eager step: buffers, kernel attributes
+            self._device_step()
+        t.cuda.current_stream(self.net.device).wait_stream(side)
+        g = t.cuda.CUDAGraph()
+        with t.cuda.graph(g):
+            self._device_step()
+        for dst, src in zip((self.net.params, self.net.m, self.net.v, self.step_dev), saved):
+            dst.copy_(src)
+        self.net._cast()
+        self.graph = g
+
+    def reset(self):
+        """Adam moments and the device step counter back to zero."""
+        self.net.m.zero_(), self.net.v.zero_(), self.step_dev.zero_()
+        self.net.step_count = 0
+
+    def run(self, lrs):
+        """len(lrs) steps, step i with learning rate lrs[i], continuing the
+        device step counter; returns the last step's loss (device tensor)."""
+        n = len(lrs)
+        done = int(self.step_dev.item())
+        if done + n > self.max_steps:
+            raise LbmError(-1, "schedule longer than max_steps")
+        table = np.full(self.max_steps, float(lrs[-1]), np.float32)
+        table[done:done + n] = np.asarray(lrs, np.float32)
+        self.lr_table.copy_(self.torch.as_tensor(table))
+        if self.graph is None:
+            self._capture()
+        for _ in range(n):
+            self.graph.replay()
+        return self.net.loss
+
 
 def cosine_lr(step, total, peak=1e-3, warmup=100, floor=0.02):
     if step < warmup:
@@ -427,16 +497,19 @@ class SurrogateRunner:
     every prediction and fall back to the method where a check fails.
 
     Checks per tube: the conservation residual of the prediction (totals of
-    mass, momentum and energy against the input state) and, on a spot-check
-    window of ``window`` nodes at a seeded offset, the L1 error against the
-    method run on that window with a margin of 2K nodes on each side (the
-    FD stencil reaches two nodes per step, so the window interior is exactly
-    what the full-tube run gives).  A tube whose residual or L1 exceeds
-    ``tol`` is recomputed by the method from the same input state.
+    mass, momentum and energy against the input state) and the L1 error on a
+    spot-check window of ``window`` nodes centred on the node where the
+    prediction changes rho most, against the method run on that window with a
+    margin of 2K nodes on each side (the FD stencil reaches two nodes per
+    step, so the window interior is exactly what the full-tube run gives).  A
+    tube whose residual or L1 exceeds ``tol``, or whose prediction is not
+    finite, is recomputed by the method from the same input state.  With
+    ``timing`` the wall time of each phase is accumulated in ``self.times``
+    (CUDA events, milliseconds).
     """
 
     def __init__(self, net: ConvOperator, n, tau, L, K, tol=1e-2, window=256, m_fd=10,
-                 seed=0, check_fraction=1.0):
+                 timing=False):
         import torch
         self.net, self.torch = net, torch
         self.n = np.asarray(n)
@@ -449,20 +522,30 @@ class SurrogateRunner:
         self.window = min(window, L - 2 * self.margin)
         if self.window < 1:
             raise LbmError(-1, "tube too short for a spot-check window")
-        self.rng = np.random.default_rng(seed)
-        nchk = max(1, int(round(check_fraction * self.B)))
-        self.check_tubes = np.sort(self.rng.choice(self.B, nchk, replace=False))
-        span = self.window + 2 * self.margin
-        self.spot = LbmBatch([span] * nchk, self.n[self.check_tubes], [tau] * nchk, mode="fd",
-                             m_fd=m_fd, device=dev)
-        self.span = span
-        self.rows = torch.as_tensor(self.check_tubes.astype(np.int64), device=dev)
-        self.off = torch.empty(nchk, dtype=torch.int32, device=dev)
-        self.gam_chk = torch.as_tensor(self.gamma_np[self.check_tubes].astype(np.float32),
-                                       device=dev)
-        self.residual = torch.empty(self.B, dtype=torch.float32, device=dev)
-        self.l1 = torch.empty(nchk, dtype=torch.float32, device=dev)
-        self.stats = {"calls": 0, "fallback_tubes": 0, "max_residual": 0.0, "max_l1": 0.0}
+        self.span = self.window + 2 * self.margin
+        B = self.B
+        self.spot = LbmBatch([self.span] * B, self.n, [tau] * B, mode="fd", m_fd=m_fd, device=dev)
+        self.rows = torch.arange(B, dtype=torch.int64, device=dev)
+        self.starts = torch.zeros(2 * B, dtype=torch.int32, device=dev)
+        self.inner = torch.full((B,), self.margin, dtype=torch.int32, device=dev)
+        self.residual = torch.empty(B, dtype=torch.float32, device=dev)
+        self.l1 = torch.empty(B, dtype=torch.float32, device=dev)
+        self.stats = {"calls": 0, "fallback_tubes": 0, "max_residual": 0.0, "max_l1": 0.0,
+                      "method_failed": 0}
+        self._solvers = {}
+        self.timing = timing
+        self.times = {}
+
+    def _mark(self, name, ev):
+        if self.timing:
+            e = self.torch.cuda.Event(enable_timing=True)
+            e.record()
+            if ev is not None:
+                prev_name, prev = ev
+                e.synchronize()
+                self.times[prev_name] = self.times.get(prev_name, 0.0) + prev.elapsed_time(e)
+            return (name, e)
+        return None
 
     def advance(self, rho, u, T):
         """One call on [B*L] device fields; returns the new fields and the
@@ -470,51 +553,79 @@ class SurrogateRunner:
         t, net, lib = self.torch, self.net, self.net.lib
         s = t.cuda.current_stream(net.device).cuda_stream
         B, L = self.B, self.L
+        ev = self._mark("predict", None)
         r2, u2, T2 = net.predict(rho, u, T, self.gamma, B, L)
+        ev = self._mark("residual", ev)
         rc = lib.lbm_nn_tube_checks(_fp(rho), _fp(u), _fp(T), _fp(r2), _fp(u2), _fp(T2),
-                                    _fp(self.half_dof), None, _fp(self.residual), None, B, L, 0, L, s)
+                                    _fp(self.half_dof), None, _fp(self.residual), None,
+                                    _fp(self.starts), self.span, self.margin, B, L, 0, L, s)
         if rc != 0:
             raise LbmError(rc, "lbm_nn_tube_checks")
-        # spot check: the method on [off - margin, off + window + margin)
-        nchk = len(self.check_tubes)
-        starts = self.rng.integers(0, L - self.span + 1, nchk).astype(np.int32)
-        self.off.copy_(t.as_tensor(starts))
-        win_in = _rows(lib, t, net.device, (rho, u, T), self.rows, self.off, self.span, L)
+        # spot check: the method on [start, start + span), compared on the
+        # interior [start + margin, start + margin + window)
+        ev = self._mark("spot_check", ev)
+        win_in = _rows(lib, t, net.device, (rho, u, T), self.rows, self.starts, self.span, L)
         self.spot.set_macro(*win_in)
         self.spot.run(self.K)
         ref = self.spot.moments()
-        off_in = t.as_tensor(starts + self.margin, device=net.device)
+        off_in = self.starts[B:]
         pred_w = _rows(lib, t, net.device, (r2, u2, T2), self.rows, off_in, self.window, L)
-        ref_w = _rows(lib, t, net.device, ref,
-                      t.arange(nchk, device=net.device, dtype=t.int64),
-                      t.full((nchk,), self.margin, dtype=t.int32, device=net.device),
-                      self.window, self.span)
+        ref_w = _rows(lib, t, net.device, ref, self.rows, self.inner, self.window, self.span)
         rc = lib.lbm_nn_tube_checks(_fp(pred_w[0]), _fp(pred_w[1]), _fp(pred_w[2]), _fp(ref_w[0]),
-                                    _fp(ref_w[1]), _fp(ref_w[2]), None, _fp(self.gam_chk), None,
-                                    _fp(self.l1), nchk, self.window, 0, self.window, s)
+                                    _fp(ref_w[1]), _fp(ref_w[2]), None, _fp(self.gamma), None,
+                                    _fp(self.l1), None, 0, 0, B, self.window, 0, self.window, s)
         if rc != 0:
             raise LbmError(rc, "lbm_nn_tube_checks")
+        ev = self._mark("decide", ev)
         res = self.residual.cpu().numpy()
         l1 = self.l1.cpu().numpy()
-        bad = ~np.isfinite(res) | (res > self.tol)
-        bad[self.check_tubes[~np.isfinite(l1) | (l1 > self.tol)]] = True
+        bad = ~np.isfinite(res) | (res > self.tol) | ~np.isfinite(l1) | (l1 > self.tol)
         fallback = np.flatnonzero(bad)
+        ev = self._mark("fallback", ev)
         if fallback.size:
             self._fallback(rho, u, T, (r2, u2, T2), fallback)
+        self._mark("end", ev)
         self.stats["calls"] += 1
         self.stats["fallback_tubes"] += int(fallback.size)
-        self.stats["max_residual"] = max(self.stats["max_residual"], float(np.nanmax(res)))
-        self.stats["max_l1"] = max(self.stats["max_l1"], float(np.nanmax(l1)))
+        fin = np.isfinite(res)
+        if fin.any():
+            self.stats["max_residual"] = max(self.stats["max_residual"], float(res[fin].max()))
+        fin = np.isfinite(l1)
+        if fin.any():
+            self.stats["max_l1"] = max(self.stats["max_l1"], float(l1[fin].max()))
         return (r2, u2, T2), fallback
 
     def _fallback(self, rho, u, T, out, tubes):
         t, net, lib = self.torch, self.net, self.net.lib
-        rows = t.as_tensor(tubes.astype(np.int64), device=net.device)
+        f = len(tubes)
+        # a pool of solvers with room for 1, 2, 4, ... tubes of length L,
+        # retargeted to the tubes of this call (lbm_batch_set_problems); the
+        # free slots repeat the last tube and their results are dropped
+        cap = 1 << (f - 1).bit_length()
+        lb = self._solvers.get(cap)
+        if lb is None:
+            lb = LbmBatch([self.L] * cap, [0] * cap, [self.tau] * cap, mode="fd", m_fd=self.m_fd,
+                          device=net.device)
+            self._solvers[cap] = lb
+        padded = np.concatenate([tubes, np.full(cap - f, tubes[-1])]).astype(np.int64)
+        lb.set_problems(self.n[padded], self.tau)
+        rows = t.as_tensor(padded, device=net.device)
         packed = _rows(lib, t, net.device, (rho, u, T), rows, None, self.L, self.L)
-        lb = LbmBatch([self.L] * len(tubes), self.n[tubes], [self.tau] * len(tubes), mode="fd",
-                      m_fd=self.m_fd, device=net.device)
         lb.set_macro(*packed)
         lb.run(self.K)
-        res = lb.moments()
+        res = [x[:f * self.L] for x in lb.moments()]
+        rows = rows[:f]
+        # where the method itself fails (non-finite or non-positive rho, T from
+        # a state at the edge of its stability), the prediction is kept and the
+        # tube is counted; everywhere else the method's result replaces it
+        st, _ = lb.status()
+        failed = np.flatnonzero(st[:f] != 0)
+        if failed.size:
+            self.stats["method_failed"] += int(failed.size)
+            good = np.flatnonzero(st[:f] == 0)
+            if good.size == 0:
+                return
+            keep = t.as_tensor(good.astype(np.int64), device=net.device)
+            res = _rows(lib, t, net.device, res, keep, None, self.L, self.L)
+            rows = t.as_tensor(tubes[good].astype(np.int64), device=net.device)
         _scatter(lib, t, net.device, res, rows, None, self.L, self.L, out)
-        lb.close()

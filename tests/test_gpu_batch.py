@@ -116,3 +116,25 @@ def test_ensemble_workload_generator_runs():
     b.run(100)
     st, bad = b.status()
     assert st.shape == (64,) and 0 <= bad <= 64
+
+
+def test_set_problems_retargets_the_ensemble():
+    """A solver created for other (n, tau) and retargeted with set_problems
+    gives the same bits as one created for the target problems."""
+    from paper_1606_06107_gb300 import LbmBatch
+    specs = SPECS[1:5]
+    rho, u, T = tubes(specs)
+    lengths = [s[0] for s in specs]
+    ref = LbmBatch(lengths, [s[1] for s in specs], [s[2] for s in specs])
+    ref.set_macro(rho, u, T)
+    ref.run(40)
+    want = [x.cpu().numpy() for x in ref.moments()]
+    b = LbmBatch(lengths, [0] * len(specs), [1.0] * len(specs))
+    b.set_macro(rho, u, T)
+    b.run(7)                     # a cached graph from before the change
+    b.set_problems([s[1] for s in specs], [s[2] for s in specs])
+    b.set_macro(rho, u, T)
+    b.run(40)
+    got = [x.cpu().numpy() for x in b.moments()]
+    for a, r in zip(got, want):
+        assert np.array_equal(a, r)
