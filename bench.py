@@ -416,7 +416,7 @@ def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int =
 
 
 def conv_leg(dev, tubes: int = 1024, L: int = 4096, patch: int = 4, C: int = 128, k: int = 5,
-             dil: int = 2, reps: int = 20):
+             dil: int = 2, reps: int = 20, impl: int = 0):
     """The surrogate's three tensor-core convolution products alone, at the
     inference shape (tubes x L/patch positions x C channels): forward with
     the fused GELU/residual epilogue, input gradient with the fused
@@ -442,16 +442,16 @@ def conv_leg(dev, tubes: int = 1024, L: int = 4096, patch: int = 4, C: int = 128
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     calls = {
         "forward": lambda: lib.lbm_nn_conv_forward(_fp(x), _fp(w), _fp(bias), _fp(y), _fp(z), tubes,
-                                                   Lp, C, k, dil, 0, _fp(st), stream),
+                                                   Lp, C, k, dil, impl, _fp(st), stream),
         "input_grad": lambda: lib.lbm_nn_conv_backward_data(_fp(x), _fp(w), _fp(gx), _fp(z),
-                                                           _fp(y), tubes, Lp, C, k, dil, 0,
+                                                           _fp(y), tubes, Lp, C, k, dil, impl,
                                                            _fp(st), stream),
         "weight_grad": lambda: lib.lbm_nn_conv_backward_weight(_fp(x), _fp(y), _fp(gw), tubes, Lp,
                                                               C, k, dil, 0, _fp(st), stream),
     }
     flops = 2.0 * P * C * C * k
     out = {"shape": f"{tubes} tubes x {Lp} positions x {C} channels, k = {k}, dilation {dil}",
-           "flops_per_launch": flops}
+           "flops_per_launch": flops, "impl": impl}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for name, fn in calls.items():
         for _ in range(3):
@@ -586,7 +586,8 @@ def run_gpu(args):
             res = batched_leg(dev, steps=args.batched_steps, count=args.batched_count,
                               sample=min(48, args.batched_count))
         elif args.only == "conv":
-            res = conv_leg(dev, tubes=args.surrogate_eval_tubes, patch=args.surrogate_patch)
+            res = conv_leg(dev, tubes=args.surrogate_eval_tubes, patch=args.surrogate_patch,
+                           impl=args.conv_impl)
         elif args.only == "surrogate":
             res = surrogate_leg(dev, train_tubes=args.surrogate_train_tubes,
                                 eval_tubes=args.surrogate_eval_tubes,
@@ -755,6 +756,8 @@ def main():
     ap.add_argument("--surrogate-windows", type=int, default=125)
     ap.add_argument("--surrogate-seconds", type=float, default=60.0)
     ap.add_argument("--surrogate-patch", type=int, default=4)
+    ap.add_argument("--conv-impl", type=int, default=0,
+                    help="convolution kernel for --only conv (include/lbm.h impl codes)")
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--batched-steps", type=int, default=4000)
     ap.add_argument("--blast-size", type=int, default=384)

@@ -405,69 +405,70 @@ __global__ void __launch_bounds__(128, 1)
 // Persistent form of the forward / input-gradient product: one block per
 // SM walks the output tiles (128 positions x 128 channels) with a stride of
 // the grid.  Warp 0 issues the TMA loads into a 4-stage ring, warp 1 issues
-// the MMAs into one of two 128-column accumulators in tensor memory, and 8
-// epilogue warps drain the other accumulator (warps 2..9: lane quarter
-// warp % 4, columns 0-63 for warps 2-5 and 64-127 for warps 6-9), so the
-// epilogue of one tile overlaps the MMAs of the next.
+// the MMAs into one of two 128-column accumulators in tensor memory, and 16
+// epilogue warps drain the other accumulator (warps 2..17: lane quarter
+// warp % 4, 32 columns each), so the epilogue of one tile overlaps the MMAs
+// of the next.
 constexpr int kPStages = 4;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;    // 4 per lane quarter, 32 accumulator columns each
 constexpr int kPThreads = 64 + 32 * kEpiWarps;
-constexpr int kStagePitch = 68;  // floats per staged row (64 + 4: conflict-free float4 rows)
+constexpr int kStagePitch = 36;  // floats per staged row (32 + 4: conflict-free float4 rows)
 constexpr int kStagingBytes = kEpiWarps * 32 * kStagePitch * 4;
 constexpr int kPSmemBytes = kPStages * kStageBytes + kStagingBytes + 1024 + 256;
 
-// Epilogue of one warp's 32 rows x 64 columns of a persistent tile.  The
-// accumulator rows (one per lane after tcgen05.ld) are transposed through a
-// padded shared-memory block so that every global load and store is done
-// cooperatively: half a warp covers the 64 columns of one row, so each
-// instruction touches two whole row segments.
-template <int EPI>
+// Epilogue of one warp's 32 rows x COLS columns (32 or 64) of a persistent
+// tile.  The accumulator rows (one per lane after tcgen05.ld) are transposed
+// through a padded shared-memory block (pitch COLS + 4 floats) so that every
+// global load and store is done cooperatively: COLS/4 lanes cover the COLS
+// columns of one row, so each instruction touches whole row segments.
+template <int EPI, int COLS = 64>
 __device__ __forceinline__ void epilogue_rows(const ConvArgs &a, float *st, uint32_t taddr, int b,
                                               int l_first, int n0, bool skip)
 {
+    constexpr int kPitch = COLS + 4, kLpr = COLS / 4, kRpi = 32 / kLpr, kBatch = 4;
     const int lane = threadIdx.x & 31;
 #pragma unroll 1
-    for (int c = 0; c < 64; c += 32) {
+    for (int c = 0; c < COLS; c += 32) {
         float v[32];
         __syncwarp();
         tmem_ld32(taddr + c, v);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            *reinterpret_cast<float4 *>(st + lane * kStagePitch + c + 4 * j) =
+            *reinterpret_cast<float4 *>(st + lane * kPitch + c + 4 * j) =
                 make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
     }
     __syncwarp();
     if (!skip) {
-        const int cg = (lane & 15) * 4;
+        const int cg = (lane % kLpr) * 4;
         float4 bias = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (EPI == kEpiForward) bias = *reinterpret_cast<const float4 *>(a.bias + n0 + cg);
-        // 16 rows per lane (r = lane/16 + 2i) in two groups of 8: all loads of
-        // a group are issued before any result is formed
+        // 32 / kRpi rows per lane (r = lane / kLpr + kRpi i) in groups of
+        // kBatch: all loads of a group are issued before any result is formed
+        const int64_t row0 = ((int64_t)b * a.L + l_first) * a.C + n0 + cg;
 #pragma unroll 1
-        for (int r0 = lane >> 4; r0 < 32; r0 += 16) {
-            float4 acc[8], gin[8];
-            uint2 in[8];
-            int64_t off[8];
-            bool live[8];
+        for (int r0 = lane / kLpr; r0 < 32; r0 += kBatch * kRpi) {
+            float4 acc[kBatch], gin[kBatch];
+            uint2 in[kBatch];
+            bool live[kBatch];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = r0 + 2 * i, l = l_first + r;
+            for (int i = 0; i < kBatch; ++i) {
+                const int r = r0 + kRpi * i, l = l_first + r;
                 live[i] = l < a.L;
-                off[i] = ((int64_t)b * a.L + l) * a.C + n0 + cg;
-                acc[i] = *reinterpret_cast<const float4 *>(st + r * kStagePitch + cg);
+                acc[i] = *reinterpret_cast<const float4 *>(st + r * kPitch + cg);
                 if (live[i]) {
+                    const int64_t o = row0 + (int64_t)(r * a.C);
                     if constexpr (EPI == kEpiForward) {
-                        in[i] = *reinterpret_cast<const uint2 *>(a.x + off[i]);
+                        in[i] = *reinterpret_cast<const uint2 *>(a.x + o);
                     } else {
-                        gin[i] = *reinterpret_cast<const float4 *>(a.gx + off[i]);
-                        if (a.gzprev) in[i] = *reinterpret_cast<const uint2 *>(a.zprev + off[i]);
+                        gin[i] = *reinterpret_cast<const float4 *>(a.gx + o);
+                        if (a.gzprev) in[i] = *reinterpret_cast<const uint2 *>(a.zprev + o);
                     }
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
+            for (int i = 0; i < kBatch; ++i) {
                 if (!live[i]) continue;
-                const int64_t o = off[i];
+                const int64_t o = row0 + (int64_t)((r0 + kRpi * i) * a.C);
                 if constexpr (EPI == kEpiForward) {
                     const float2 x01 =
                         __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&in[i].x));
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
         }
     } else {  // epilogue warps
-        const int e = warp - 2, quarter = warp & 3, col0 = (e >> 2) * 64;
+        const int e = warp - 2, quarter = warp & 3, col0 = (e >> 2) * 32;
         int it = 0;
         for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
             const int acc = it & 1, use = it >> 1;
@@ -617,9 +618,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
             __syncwarp();
             if (!ready) failed = 1;
             tc_fence_after();
-            epilogue_rows<EPI>(a, staging + e * 32 * kStagePitch,
-                               tmem + acc * kTile + ((uint32_t)(quarter * 32) << 16) + col0, b,
-                               l0 + quarter * 32, n0 + col0, failed != 0);
+            epilogue_rows<EPI, 32>(a, staging + e * 32 * kStagePitch,
+                                   tmem + acc * kTile + ((uint32_t)(quarter * 32) << 16) + col0, b,
+                                   l0 + quarter * 32, n0 + col0, failed != 0);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&tempty[acc]))
