@@ -427,3 +427,51 @@ def test_graph_training_step_equals_eager(lbmlib):
     # Adam's first step is lr * g / (|g| + eps): equal wherever the gradient's
     # sign is not decided by the reduction order
     assert np.mean(np.abs(p0 - p1) <= 1e-6) > 0.999
+
+
+def test_trained_network_gains_over_the_method_alone(lbmlib):
+    """What training buys: after a short run of graph-replayed steps on
+    restarted-method pairs of 24 tubes, one call of the network on 8
+    held-out tubes lands far closer to the method's own K-step result than
+    the state it started from (the only prediction available without the
+    network), and inside the stated 1e-2; the checked runner's result for
+    the same call is within the tolerance on every tube."""
+    torch = _t()
+    from paper_1606_06107_gb300 import workloads
+    from paper_1606_06107_gb300.surrogate import (ConvOperator, SurrogateRunner, Trainer,
+                                                  cosine_lr, output_scales,
+                                                  restarted_trajectories)
+    L, K = 1024, 32
+
+    def tubes(count, seed):
+        wls = workloads.surrogate_tubes(count=count, L=L, seed=seed)
+        return ([np.concatenate([w.rho for w in wls]), np.concatenate([w.u[0] for w in wls]),
+                 np.concatenate([w.T for w in wls])], np.array([w.n for w in wls]), wls[0].tau)
+
+    (r, u, T), n, tau = tubes(24, 0)
+    tr = restarted_trajectories(r, u, T, n, tau, L, K, windows=16)
+    (r, u, T), n_ev, _ = tubes(8, 1)
+    ev = restarted_trajectories(r, u, T, n_ev, tau, L, K, windows=6)
+    net = ConvOperator(C=128, dilations=(1, 1, 2, 2, 4, 4), patch=4, out_scale=output_scales(tr),
+                       seed=0)
+    trainer = Trainer(net, tr, batch=16, seed=0, max_steps=4096)
+    steps = 3000
+    trainer.run([cosine_lr(i, steps, peak=1e-3, warmup=100) for i in range(steps)])
+    torch.cuda.synchronize()
+    net.check_status()
+    gam = torch.as_tensor(ev.gamma.astype(np.float32), device="cuda")
+    ok = ev.ok
+    assert ok.sum() >= 4
+    j = 3
+    s0 = [f[j] for f in (ev.rho, ev.u, ev.T)]
+    ref = [host(f[j + 1]).reshape(8, L) for f in (ev.rho, ev.u, ev.T)]
+    pred = [host(x).reshape(8, L) for x in net.predict(*s0, gam, 8, L)]
+    start = [host(x).reshape(8, L) for x in s0]
+    e_net = S.l1_error(*pred, *ref, ev.gamma)[ok]
+    e_id = S.l1_error(*start, *ref, ev.gamma)[ok]
+    assert np.all(e_net < 0.25 * e_id), (e_net, e_id)
+    assert np.all(e_net < 1e-2)
+    run = SurrogateRunner(net, n_ev, tau, L, K, window=256)
+    out, _ = run.advance(*[x.clone() for x in s0])
+    e_run = S.l1_error(*[host(x).reshape(8, L) for x in out], *ref, ev.gamma)[ok]
+    assert np.all(e_run <= 1e-2)
