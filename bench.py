@@ -402,6 +402,7 @@ def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int =
             "l1_identity_after_rollout": {"median": q(e_id, 50), "max": q(e_id, 100)},
             "phase_ms_per_call": phases,
             "fallback_tubes": stats["fallback_tubes"],
+            "method_failed_tubes": int(run.quarantined.sum()),
             "fallback_fraction": stats["fallback_tubes"] / ((windows + 1) * eval_tubes),
             "max_spot_l1": stats["max_l1"],
             "training": {"pairs": int(train_tubes * windows), "steps": total,

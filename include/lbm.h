@@ -322,7 +322,8 @@ int lbm_nn_cast_weights(const float *w, void *w_bf16, void *wt_bf16, int layers,
                         void *stream);
 
 /* Lift: x0[p][c] = bf16(sum_j feat[p][j] Wl[c][j] + bl[c]) for P positions
- * of F <= 64 float features; C <= 256. */
+ * of F float features, F one of 4, 8, 16, 32 (patches of 1, 2, 4, 8 nodes),
+ * feat and Wl 16-byte aligned; C a multiple of 32, at most 1024. */
 int lbm_nn_lift(const float *feat, const float *Wl, const float *bl, void *x0, int64_t P, int F,
                 int C, void *stream);
 
@@ -332,8 +333,9 @@ int lbm_nn_lift(const float *feat, const float *Wl, const float *bl, void *x0, i
 int lbm_nn_lift_backward(const float *gx0, const float *feat, float *gWl, float *gbl, int64_t P,
                          int F, int C, void *stream);
 
-/* Head: out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o], Fo <= 16 float outputs,
- * C a multiple of 32, at most 256. */
+/* Head: out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o] for Fo = 3, 6 or 12 float
+ * outputs (patches of 1, 2, 4 nodes); C a multiple of 8, at most 1024; x and
+ * Wp 16-byte aligned. */
 int lbm_nn_head(const void *x, const float *Wp, const float *bp, float *out, int64_t P, int C, int Fo,
                 void *stream);
 

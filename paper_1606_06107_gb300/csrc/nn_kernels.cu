@@ -839,48 +839,83 @@ int grid_for(int64_t n, int threads = 256)
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 16));
 }
 
-// x0[p][c] = bf16(sum_j feat[p][j] Wl[c][j] + bl[c]); F <= 64 features.  The
-// weights sit transposed in shared memory (wsh[j][c]) so that the threads of
-// a warp, which take consecutive channels, read consecutive banks.
+// x0[p][c] = bf16(sum_j feat[p][j] Wl[c][j] + bl[c]).  Thread c of a block of
+// C threads keeps row c of the weights in registers and walks a range of
+// positions; the F features of a position are one broadcast load per warp
+// (float4s) and the C outputs of a position one coalesced row.
+template <int F>
 __global__ void k_lift(const float *feat, const float *Wl, const float *bl, __nv_bfloat16 *x0,
-                       int64_t P, int F, int C)
+                       int64_t P, int C, int64_t per_block)
 {
-    extern __shared__ float wsh[];  // [F][C] then [C]
-    for (int i = threadIdx.x; i < C * F; i += blockDim.x) wsh[(i % F) * C + i / F] = Wl[i];
-    for (int i = threadIdx.x; i < C; i += blockDim.x) wsh[C * F + i] = bl[i];
-    __syncthreads();
-    const int64_t n = P * C;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = i / C;
-        const int c = (int)(i - p * C);
-        const float *f = feat + p * F;
-        float s = wsh[C * F + c];
-        for (int j = 0; j < F; ++j) s = fmaf(__ldg(f + j), wsh[j * C + c], s);
-        x0[i] = __float2bfloat16_rn(s);
+    const int c = threadIdx.x;
+    float w[F];
+#pragma unroll
+    for (int j = 0; j < F / 4; ++j) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(Wl + c * F) + j);
+        w[4 * j] = q.x, w[4 * j + 1] = q.y, w[4 * j + 2] = q.z, w[4 * j + 3] = q.w;
+    }
+    const float bias = bl[c];
+    const int64_t p0 = blockIdx.x * per_block, p1 = std::min(P, p0 + per_block);
+    constexpr int G = 4;  // positions whose feature loads are in flight together
+    for (int64_t p = p0; p < p1; p += G) {
+        float4 v[G][F / 4];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int j = 0; j < F / 4; ++j)
+                v[g][j] = p + g < p1 ? __ldg(reinterpret_cast<const float4 *>(feat + (p + g) * F) + j)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (p + g >= p1) break;
+            float acc = bias;
+#pragma unroll
+            for (int j = 0; j < F / 4; ++j) {
+                acc = fmaf(v[g][j].x, w[4 * j], acc);
+                acc = fmaf(v[g][j].y, w[4 * j + 1], acc);
+                acc = fmaf(v[g][j].z, w[4 * j + 2], acc);
+                acc = fmaf(v[g][j].w, w[4 * j + 3], acc);
+            }
+            x0[(p + g) * C + c] = __float2bfloat16_rn(acc);
+        }
     }
 }
 
-// out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o]: one warp per position, each
-// lane holding channels lane + 32 j (C <= 256), reduced by shuffles.
+// out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o]: one thread per position reads
+// its row of C bf16 values as 16-byte vectors; the FO x C weights sit in
+// shared memory and are read as warp-wide broadcasts.
+template <int FO>
 __global__ void k_head(const __nv_bfloat16 *x, const float *Wp, const float *bp, float *out,
-                       int64_t P, int C, int Fo)
+                       int64_t P, int C)
 {
-    const int lane = threadIdx.x & 31, nj = C / 32;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
+    extern __shared__ float wsh[];  // [FO][C]
+    for (int i = threadIdx.x; i < FO * C; i += blockDim.x) wsh[i] = Wp[i];
+    __syncthreads();
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float acc[FO];
+#pragma unroll
+    for (int o = 0; o < FO; ++o) acc[o] = __ldg(bp + o);
+    const uint4 *row = reinterpret_cast<const uint4 *>(x + p * C);
+    for (int c8 = 0; c8 < C / 8; ++c8) {
         float xv[8];
+        unpack8(__ldg(row + c8), xv);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) xv[j] = j < nj ? __bfloat162float(x[p * C + lane + 32 * j]) : 0.f;
-        for (int o = 0; o < Fo; ++o) {
-            float s = 0.f;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (j < nj) s = fmaf(xv[j], __ldg(Wp + o * C + lane + 32 * j), s);
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == o) out[p * Fo + o] = s + bp[o];
+        for (int o = 0; o < FO; ++o) {
+            const float4 w0 = *reinterpret_cast<const float4 *>(wsh + o * C + 8 * c8);
+            const float4 w1 = *reinterpret_cast<const float4 *>(wsh + o * C + 8 * c8 + 4);
+            acc[o] = fmaf(xv[0], w0.x, acc[o]);
+            acc[o] = fmaf(xv[1], w0.y, acc[o]);
+            acc[o] = fmaf(xv[2], w0.z, acc[o]);
+            acc[o] = fmaf(xv[3], w0.w, acc[o]);
+            acc[o] = fmaf(xv[4], w1.x, acc[o]);
+            acc[o] = fmaf(xv[5], w1.y, acc[o]);
+            acc[o] = fmaf(xv[6], w1.z, acc[o]);
+            acc[o] = fmaf(xv[7], w1.w, acc[o]);
         }
     }
+#pragma unroll
+    for (int o = 0; o < FO; ++o) out[p * FO + o] = acc[o];
 }
 
 // Head backward: gx = gout Wp; gz = bf16(gx gelu'(z)); gWp += gout^T x; gbp += sum gout.
@@ -1441,12 +1476,21 @@ int lbm_nn_cast_weights(const float *w, void *w_bf16, void *wt_bf16, int layers,
 int lbm_nn_lift(const float *feat, const float *Wl, const float *bl, void *x0, int64_t P, int F,
                 int C, void *stream)
 {
-    if (!feat || !Wl || !bl || !x0 || P < 1 || F < 1 || F > 64 || C < 1 || C > 256 ||
-        (size_t)(C * F + C) * sizeof(float) > 48 * 1024)
+    if (!feat || !Wl || !bl || !x0 || P < 1 || C < 32 || C > 1024 || C % 32 ||
+        (F != 4 && F != 8 && F != 16 && F != 32) || !aligned16(feat) || !aligned16(Wl))
         return LBM_EINVAL;
-    const size_t sh = (size_t)(C * F + C) * sizeof(float);
-    k_lift<<<grid_for(P * C), 256, sh, (cudaStream_t)stream>>>(feat, Wl, bl, (__nv_bfloat16 *)x0, P,
-                                                               F, C);
+    const int64_t per_block = 256;
+    const int64_t nblocks = (P + per_block - 1) / per_block;
+    if (nblocks > 0x7fffffff) return LBM_EINVAL;
+    const int blocks = (int)nblocks;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto out = (__nv_bfloat16 *)x0;
+    switch (F) {
+    case 4: k_lift<4><<<blocks, C, 0, s>>>(feat, Wl, bl, out, P, C, per_block); break;
+    case 8: k_lift<8><<<blocks, C, 0, s>>>(feat, Wl, bl, out, P, C, per_block); break;
+    case 16: k_lift<16><<<blocks, C, 0, s>>>(feat, Wl, bl, out, P, C, per_block); break;
+    default: k_lift<32><<<blocks, C, 0, s>>>(feat, Wl, bl, out, P, C, per_block); break;
+    }
     return launched(cudaGetLastError());
 }
 
@@ -1471,10 +1515,17 @@ int lbm_nn_lift_backward(const float *gx0, const float *feat, float *gWl, float 
 int lbm_nn_head(const void *x, const float *Wp, const float *bp, float *out, int64_t P, int C, int Fo,
                 void *stream)
 {
-    if (!x || !Wp || !bp || !out || P < 1 || C < 32 || C > 256 || C % 32 || Fo < 1 || Fo > 16)
+    if (!x || !Wp || !bp || !out || P < 1 || C < 8 || C > 1024 || C % 8 || !aligned16(x) ||
+        !aligned16(Wp) || (Fo != 3 && Fo != 6 && Fo != 12))
         return LBM_EINVAL;
-    k_head<<<grid_for(P * 32), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)x, Wp, bp, out,
-                                                               P, C, Fo);
+    const int64_t nblocks = (P + 127) / 128;
+    if (nblocks > 0x7fffffff) return LBM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto xb = (const __nv_bfloat16 *)x;
+    const size_t sh = sizeof(float) * Fo * C;
+    if (Fo == 3) k_head<3><<<(int)nblocks, 128, sh, s>>>(xb, Wp, bp, out, P, C);
+    else if (Fo == 6) k_head<6><<<(int)nblocks, 128, sh, s>>>(xb, Wp, bp, out, P, C);
+    else k_head<12><<<(int)nblocks, 128, sh, s>>>(xb, Wp, bp, out, P, C);
     return launched(cudaGetLastError());
 }
 

@@ -503,7 +503,9 @@ class SurrogateRunner:
     margin of 2K nodes on each side (the FD stencil reaches two nodes per
     step, so the window interior is exactly what the full-tube run gives).  A
     tube whose residual or L1 exceeds ``tol``, or whose prediction is not
-    finite, is recomputed by the method from the same input state.  With
+    finite, is recomputed by the method from the same input state; a tube on
+    which the method itself fails (non-finite or non-positive rho, T) keeps
+    the prediction and is not sent to the method again (``quarantined``).  With
     ``timing`` the wall time of each phase is accumulated in ``self.times``
     (CUDA events, milliseconds).
     """
@@ -532,6 +534,7 @@ class SurrogateRunner:
         self.l1 = torch.empty(B, dtype=torch.float32, device=dev)
         self.stats = {"calls": 0, "fallback_tubes": 0, "max_residual": 0.0, "max_l1": 0.0,
                       "method_failed": 0}
+        self.quarantined = np.zeros(self.B, dtype=bool)
         self._solvers = {}
         self.timing = timing
         self.times = {}
@@ -580,7 +583,8 @@ class SurrogateRunner:
         res = self.residual.cpu().numpy()
         l1 = self.l1.cpu().numpy()
         bad = ~np.isfinite(res) | (res > self.tol) | ~np.isfinite(l1) | (l1 > self.tol)
-        fallback = np.flatnonzero(bad)
+        # a tube on which the method itself has failed is not sent back to it
+        fallback = np.flatnonzero(bad & ~self.quarantined)
         ev = self._mark("fallback", ev)
         if fallback.size:
             self._fallback(rho, u, T, (r2, u2, T2), fallback)
@@ -622,6 +626,7 @@ class SurrogateRunner:
         failed = np.flatnonzero(st[:f] != 0)
         if failed.size:
             self.stats["method_failed"] += int(failed.size)
+            self.quarantined[tubes[failed]] = True
             good = np.flatnonzero(st[:f] == 0)
             if good.size == 0:
                 return
