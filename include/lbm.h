@@ -268,8 +268,9 @@ void lbm_batch_destroy(lbm_batch b);
  * Learned surrogate: a 1-D convolutional operator that advances the
  * macroscopic state (rho, u, T) of a tube by K lattice steps per call.  The
  * paper has no counterpart: it is an extension of the method, which remains
- * its fallback and its judge.  The network (all entry points below are its
- * building blocks; the layer sequence is driven by the Python binding):
+ * its fallback and the reference it is measured against.  The network (all
+ * entry points below are its building blocks; the layer sequence is driven
+ * by the Python binding):
  *   features  a[p]     = ((rho-1)/s0, u/s1, (T-1)/s2, (gamma-1.4)/s3)
  *   lift      x0       = bf16(a Wl^T + bl)
  *   layer i   z_i      = conv(x_i; W_i, d_i) + b_i,  W_i[t][co][ci], k taps,

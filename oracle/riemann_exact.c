@@ -1,6 +1,6 @@
 /*
  * riemann_exact.c -- exact solution of the 1-D Riemann problem for the Euler
- * equations of an ideal gas, used to judge the shock-tube runs (Sec. VI: the
+ * equations of an ideal gas, used to check the shock-tube runs (Sec. VI: the
  * paper compares with the analytic solution of Sod's problem but does not
  * print it).
  *

@@ -1,8 +1,8 @@
 // Kernels of the learned surrogate: a 1-D convolutional operator over tubes
 // that advances the macroscopic state (rho, u, T) by K lattice steps per call
 // (the lbm_nn_* entry points of include/lbm.h).  The paper has no such
-// network; it is an extension whose fallback and judge is the lattice
-// Boltzmann method itself.
+// network; it is an extension whose fallback, and the reference it is
+// measured against, is the lattice Boltzmann method itself.
 //
 // Data layout (channel-last, one tube after another):
 //   activations x[b][l][c] bfloat16, C channels (C a multiple of 128);

@@ -1,7 +1,7 @@
 """Learned surrogate of the 1-D method: a convolutional operator that advances
 the macroscopic state (rho, u, T) of shock tubes by K lattice steps per call,
 trained on the GPU on trajectories the lattice Boltzmann solver generates,
-with that solver as its fallback and judge.
+with that solver as its fallback and the reference it is measured against.
 
 Argument marshalling only: the network, its training and every check run in
 the CUDA kernels behind the ``lbm_nn_*`` entry points of ``liblbm.so``;
