@@ -162,6 +162,14 @@ int lbm_conservation(lbm_handle h, double *out);
  * than 256 SMs), LBM_EINVAL for null or misaligned pointers. */
 int lbm_conservation_noalloc(lbm_handle h, const void *state, void *stream, double *out);
 
+/* Sampled read-back of the current state: for `count` (<= 2^20) nodes
+ * given by their indices node = x + X (y + Y z) in the device array `nodes`
+ * (int64; the caller keeps them below X*Y*Z), writes all Q + Q_r populations,
+ * decoded to float, to the device array out[k * (Q + Q_r) + i] (translational
+ * i < Q first, then the rotational ones).  For checks of states too large to
+ * copy back whole.  Asynchronous. */
+int lbm_sample_state(lbm_handle h, const int64_t *nodes, int count, float *out);
+
 /* Copy the stored populations to / from device arrays in canonical order:
  * ft[i*N + node] for i < Q_t, fr[j*N + node] for j < Q_r (fr ignored when
  * n = 0).  In STREAM mode ft holds post-collision values (the pull source).

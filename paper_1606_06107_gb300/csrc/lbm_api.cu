@@ -563,6 +563,22 @@ int lbm_get_state(lbm_handle h, float *ft, float *fr)
     return LBM_OK;
 }
 
+int lbm_sample_state(lbm_handle h, const int64_t *nodes, int count, float *out)
+{
+    if (!h) return LBM_EINVAL;
+    if (!h->has_state) return fail(h, LBM_ESTATE, "no state");
+    if (!nodes || !out || count < 1 || count > (1 << 20)) return fail(h, LBM_EINVAL, "bad sample");
+    DeviceGuard g(h->device);
+    Args a = make_args(h);
+    a.src = static_cast<const float *>(h->buf[h->cur]);
+    a.nodes = nodes;
+    a.count = count;
+    a.out0 = out;
+    cudaError_t e = launch(h, Op::Sample, a);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sample kernel");
+    return LBM_OK;
+}
+
 int lbm_set_state(lbm_handle h, const float *ft, const float *fr)
 {
     if (!h) return LBM_EINVAL;

@@ -17,7 +17,7 @@ constexpr size_t kWorkResult = 256;    // kRedSlots doubles: finished reduction
 constexpr size_t kWorkPartials = 512;  // kMaxRedBlocks * kRedSlots doubles
 constexpr size_t kWorkBytes = kWorkPartials + sizeof(double) * kRedSlots * kMaxRedBlocks;
 
-enum class Op { Step, Init, Moments, Conserve, GetState, SetState };
+enum class Op { Step, Init, Moments, Conserve, GetState, SetState, Sample };
 
 // Everything a kernel launch needs; filled by the host API.
 struct Args {
@@ -37,6 +37,8 @@ struct Args {
     int *status;
     double *partials;
     int red_blocks;
+    const int64_t *nodes;  // Sample: node indices (x fastest), `count` of them
+    int count;
 };
 
 cudaError_t launch_d1q7(Op op, const Args &a, cudaStream_t s);

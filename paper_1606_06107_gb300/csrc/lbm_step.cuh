@@ -148,6 +148,8 @@ template <int Q, typename ST = float> struct Params {
     float *out0, *out1, *out2;
     int *status;
     double *partials;
+    const int64_t *nodes;
+    int count;
     int64_t S, N;
     int X, Y, Z, pitch;
     int bc0, bc1, bc2;
@@ -165,6 +167,8 @@ template <int Q, typename ST = float> Params<Q, ST> make_params(const Args &a)
     p.out0 = a.out0; p.out1 = a.out1; p.out2 = a.out2;
     p.status = a.status;
     p.partials = a.partials;
+    p.nodes = a.nodes;
+    p.count = a.count;
     p.S = a.S;
     p.N = a.N;
     p.X = a.X; p.Y = a.Y; p.Z = a.Z; p.pitch = a.pitch;
@@ -791,6 +795,21 @@ __global__ void __launch_bounds__(kBlockX) k_get_state(const Params<Lattice<LAT>
         for (int j = 0; j < 7; ++j) p.out1[(int64_t)j * p.N + node] = ld(p, L::Q + j, self);
 }
 
+// Sampled read-back: out0[k * (Q + Qr) + i] = population i of node nodes[k]
+// (decoded to float), for checks at sizes too large to copy back whole.
+template <int LAT, bool ROT, typename ST>
+__global__ void k_sample(const Params<Lattice<LAT>::Q, ST> p)
+{
+    constexpr int Q = Lattice<LAT>::Q, QA = Q + (ROT ? 7 : 0);
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)p.count * QA) return;
+    const int k = (int)(e / QA), i = (int)(e % QA);
+    const int64_t node = p.nodes[k];
+    const int x = (int)(node % p.X), y = (int)((node / p.X) % p.Y), z = (int)(node / ((int64_t)p.X * p.Y));
+    const int self = (z * p.Y + y) * p.pitch + x;
+    p.out0[e] = ld(p, i, self);
+}
+
 template <int LAT, bool ROT, typename ST>
 __global__ void __launch_bounds__(kBlockX) k_set_state(const Params<Lattice<LAT>::Q, ST> p)
 {
@@ -830,6 +849,11 @@ cudaError_t launch_mode(Op op, const Args &a, cudaStream_t s)
     case Op::Conserve: k_conserve<LAT, ROT, MODE><<<a.red_blocks, kRedThreads, 0, s>>>(p); break;
     case Op::GetState: k_get_state<LAT, ROT><<<grid, block, 0, s>>>(p); break;
     case Op::SetState: k_set_state<LAT, ROT><<<grid, block, 0, s>>>(p); break;
+    case Op::Sample: {
+        const int64_t n = (int64_t)a.count * (Lattice<LAT>::Q + (ROT ? 7 : 0));
+        k_sample<LAT, ROT><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
+        break;
+    }
     }
     return cudaGetLastError();
 }

@@ -44,6 +44,7 @@ SIGNATURES = {
     "lbm_conservation_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "lbm_get_state": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbm_set_state": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lbm_sample_state": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
     "lbm_status": (ctypes.c_int, [_vp]),
     "lbm_steps": (_i64, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
@@ -269,6 +270,17 @@ class Lbm:
             b = self._field(fr, self.Qr) if self.Qr else t.zeros(1, device=self.device)
             self._keep = (a, b)
             self._check(self.lib.lbm_set_state(self.h, a.data_ptr(), b.data_ptr()))
+
+    def sample(self, nodes):
+        """All populations of the given nodes (indices x + X (y + Y z)) as a
+        [len(nodes), Q + Qr] float32 array (lbm_sample_state)."""
+        t = self.torch
+        with t.cuda.device(self.device):
+            idx = t.as_tensor(np.asarray(nodes, dtype=np.int64), device=self.device)
+            out = t.empty((idx.numel(), self.Q + self.Qr), dtype=t.float32, device=self.device)
+            self._check(self.lib.lbm_sample_state(self.h, idx.data_ptr(), idx.numel(),
+                                                  out.data_ptr()))
+            return out.cpu().numpy()
 
     def status(self) -> int:
         with self.torch.cuda.device(self.device):

@@ -74,3 +74,78 @@ def test_stated_blast_is_flagged_not_trapped():
     g.set_macro(wl.rho, wl.u, wl.T)
     g.step(30)
     assert g.status() == -4
+
+
+def test_full_size_blast_config_sampled(orc):
+    """The 3-D blast leg's configuration at full size (384^3, D3Q343, n = 0,
+    f16 deviation storage, periodic, the launch bench.py times): after two
+    steps from the equilibrium state, every population of sampled nodes (on
+    the sphere's edge, where neighbours differ, in the interior and at the
+    periodic wrap) equals the oracle's BGK collision of the populations
+    pulled from the neighbours' equilibria, within the f16 storage
+    rounding."""
+    from paper_1606_06107_gb300 import Lbm
+    L = 384
+    wl = workloads.blast_3d(L=L, radius=32.0, n=0, p_in=1.5, p_out=0.5)
+    g = Lbm("D3Q343", 0, wl.tau, wl.shape, wl.bc, storage="f16")
+    g.set_macro(wl.rho, wl.u, wl.T)
+    g.step(2)
+    assert g.status() == 0
+    rng = np.random.default_rng(3)
+    c = L / 2.0
+    picks = []
+    while len(picks) < 16:                           # sphere edge: radius 30..34
+        x, y, z = rng.integers(0, L, 3)
+        if 30.0 <= np.sqrt((x + .5 - c) ** 2 + (y + .5 - c) ** 2 + (z + .5 - c) ** 2) <= 34.0:
+            picks.append((x, y, z))
+    picks += [tuple(rng.integers(0, L, 3)) for _ in range(4)]
+    picks += [(0, 0, 0), (L - 1, 0, L - 1), (0, L - 1, 1), (L - 1, L - 1, L - 1)]
+    nodes = [x + L * (y + L * z) for x, y, z in picks]
+    got = g.sample(nodes)                            # [k, 343]
+    r, e, w, _ = orc.lattice(orc.D3Q343)
+    xi = r * e.astype(np.float64)
+    omega = 1.0 / wl.tau
+    u16 = 2.0 ** -11                                 # f16 half-ulp, relative
+    rho32 = wl.rho.astype(np.float32).astype(np.float64)
+    T32 = wl.T.astype(np.float32).astype(np.float64)
+    cache = {}
+
+    def eq(rho, u, T):
+        return orc.geq(orc.D3Q343, rho, u, T)
+
+    for k, (x, y, z) in enumerate(picks):
+        pulled = np.empty(343)
+        for i in range(343):                         # g_i(x) = ft*_i(x - e_i) = g_i^eq(m0(x - e_i))
+            xs, ys, zs = (x - e[i, 0]) % L, (y - e[i, 1]) % L, (z - e[i, 2]) % L
+            key = (rho32[zs, ys, xs], T32[zs, ys, xs])
+            if key not in cache:
+                cache[key] = eq(key[0], [0.0, 0.0, 0.0], key[1])
+            pulled[i] = cache[key][i]
+        want, _ = orc.collide_node(orc.D3Q343, 0, omega, pulled, None)
+        # Error bound, first order.  Each pulled value carries two f16
+        # roundings of its deviation d = f/w - 1 (the initial state, the store
+        # after step 1): eps_j = 2 u16 w_j |d_j|.  They move the node's
+        # moments by at most |d rho| = sum eps, |d u_a| = sum |xi_a - u_a| eps
+        # / rho, |d T| = sum ||xi - u|^2/3 - T| eps / rho, which move g^eq by
+        # its sensitivities (central differences of the oracle's g^eq); BGK
+        # passes (1 - omega) of eps and omega of the g^eq change; the final
+        # store adds one more rounding.  Float32 arithmetic and the moment
+        # corrections add ~1e-6 of the largest population.
+        eps = 2 * u16 * np.abs(pulled - w)
+        rho, u, T, _, _ = orc.node_moments(orc.D3Q343, 0, pulled, None)
+        dx = xi - u
+        d_rho = eps.sum()
+        d_u = (np.abs(dx) * eps[:, None]).sum(0) / rho
+        d_T = (np.abs((dx * dx).sum(1) / 3.0 - T) * eps).sum() / rho
+        h = 1e-6
+        sens = np.abs(eq(rho + h, u, T) - eq(rho - h, u, T)) / (2 * h) * d_rho
+        for a in range(3):
+            up, dn = np.array(u, float), np.array(u, float)
+            up[a] += h
+            dn[a] -= h
+            sens += np.abs(eq(rho, up, T) - eq(rho, dn, T)) / (2 * h) * d_u[a]
+        sens += np.abs(eq(rho, u, T + h) - eq(rho, u, T - h)) / (2 * h) * d_T
+        tol = ((1 - omega) * eps + omega * sens + u16 * np.abs(want - w)
+               + 1e-6 * np.abs(want).max())
+        ratio = np.abs(got[k] - want) / tol
+        assert np.all(ratio <= 1.0), (picks[k], ratio.max(), int(ratio.argmax()))
