@@ -538,6 +538,24 @@ def dist_setup(n_gpus):
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of the ranks' values (the job's wall time is the slowest
+    replica's); the identity on one rank."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(nodes: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job Mnode-updates/s: every replica advances `nodes` nodes `steps`
+    times; the job takes the slowest replica's time."""
+    return nodes * steps * world / seconds / 1e6
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args.gpus)
     if rank != 0:
@@ -642,14 +660,9 @@ def run_gpu(args):
     per_launch = [s.elapsed_time(e) / 1e3 for s, e in zip(starts, ends)]
     status = sim.status()
 
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-
+    elapsed = max_over_ranks(elapsed, world, dev)
     nodes = X * Y
-    value = nodes * args.steps * world / elapsed / 1e6
+    value = job_throughput(nodes, args.steps, world, elapsed)
     hbm, peak_kind = peaks()
     avg_launch = float(np.mean(per_launch))
     achieved = BYTES_PER_NODE * nodes / avg_launch / 1e9
@@ -677,13 +690,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_dt = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_dt = float(t.item())
+    e2e_dt = max_over_ranks(e2e_dt, world, dev)
     field_bytes = 4 * nodes * 4  # rho, u_x, u_y, T
-    e2e = {"value": nodes * e2e_steps * world / e2e_dt / 1e6, "unit": "Mnode-updates/s",
+    e2e = {"value": job_throughput(nodes, e2e_steps, world, e2e_dt), "unit": "Mnode-updates/s",
            "h2d_bytes_per_step": field_bytes / e2e_steps,
            "d2h_bytes_per_step": 4 + field_bytes / e2e_steps}
 
