@@ -422,6 +422,15 @@ int lbm_nn_tube_checks(const float *rho, const float *u, const float *T, const f
                        float *residual, float *l1, int *starts, int span, int margin, int B, int L,
                        int w0, int W, void *stream);
 
+/* Self-test of the bounded barrier wait the tensor-core kernels use (a
+ * library service, no counterpart in the paper): one thread waits on a
+ * shared-memory barrier that nothing completes unless `arrive` is set; after
+ * budget_cycles (<= 2^34) clock cycles the wait gives up and sets bit 4 of
+ * the device int *status, exactly as a stalled convolution kernel would.
+ * Lets a test confirm, without faulting or hanging the GPU, that such a
+ * stall ends in a status the host can read. */
+int lbm_nn_wait_selftest(long long budget_cycles, int arrive, int *status, void *stream);
+
 /* Row gather of three float fields stored as rows of row_len nodes:
  * d_f[i*W + w] = f[rows[i]*row_len + offsets[i] + w] for i < count, w < W
  * (rows: device int64, offsets: device int or NULL for 0).  Used for the

@@ -120,18 +120,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Wait for the phase of `bar` with the given parity to complete; gives up
-// after kWaitCycles, sets the timeout bit and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status)
+// after `budget` clock cycles (kWaitCycles by default), sets the timeout bit
+// and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status,
+                                          long long budget = kWaitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > budget) {
             if (status) atomicOr(status, kTimeoutBit);
             return false;
         }
     }
     return true;
+}
+
+// Self-test of the bounded wait: one thread waits on a barrier that only it
+// could complete (it arrives first when `arrive` is set); otherwise nothing
+// arrives and the wait must give up after `budget` cycles.
+__global__ void k_wait_selftest(long long budget, int arrive, int *status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&bar)) : "memory");
+    mbar_wait(&bar, 0, status, budget);
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
@@ -1657,6 +1672,13 @@ int lbm_nn_tube_checks(const float *rho, const float *u, const float *T, const f
     return launched(cudaGetLastError());
 }
 
+
+int lbm_nn_wait_selftest(long long budget_cycles, int arrive, int *status, void *stream)
+{
+    if (!status || budget_cycles < 0 || budget_cycles > (1ll << 34)) return LBM_EINVAL;
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(budget_cycles, arrive, status);
+    return launched(cudaGetLastError());
+}
 
 int lbm_nn_gather(const float *a, const float *b, const float *c, const int64_t *rows,
                   const int *offsets, int count, int64_t row_len, int W, float *da, float *db,

@@ -105,6 +105,7 @@ SIGNATURES = {
     "lbm_nn_targets": (ctypes.c_int, [_vp] * 7 + [_i64, ctypes.POINTER(ctypes.c_float), _vp]),
     "lbm_nn_apply": (ctypes.c_int, [_vp] * 7 + [_i64, ctypes.POINTER(ctypes.c_float), _vp]),
     "lbm_nn_tube_checks": (ctypes.c_int, [_vp] * 11 + [ctypes.c_int] * 6 + [_vp]),
+    "lbm_nn_wait_selftest": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _vp, _vp]),
     "lbm_nn_gather": (ctypes.c_int, [_vp] * 5 + [ctypes.c_int, _i64, ctypes.c_int]
                       + [_vp] * 4),
     "lbm_nn_scatter": (ctypes.c_int, [_vp] * 5 + [ctypes.c_int, _i64, ctypes.c_int]

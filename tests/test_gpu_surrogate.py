@@ -476,3 +476,19 @@ def test_trained_network_gains_over_the_method_alone(lbmlib):
     out, _ = run.advance(*[x.clone() for x in s0])
     e_run = S.l1_error(*[host(x).reshape(8, L) for x in out], *ref, ev.gamma)[ok]
     assert np.all(e_run <= 1e-2)
+
+
+def test_bounded_wait_gives_up_and_reports(lbmlib):
+    """A barrier nothing completes: the wait gives up after its budget, sets
+    the timeout bit the host reads, and the context stays usable; with the
+    arrival the same wait succeeds and leaves the status alone."""
+    torch = _t()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lbmlib.lbm_nn_wait_selftest(1 << 21, 0, vp(st), stream()) == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 4
+    st.zero_()
+    assert lbmlib.lbm_nn_wait_selftest(1 << 21, 1, vp(st), stream()) == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert float(torch.ones(4, device="cuda").sum().item()) == 4.0
