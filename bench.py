@@ -605,8 +605,7 @@ def run_gpu(args):
             res = batched_leg(dev, steps=args.batched_steps, count=args.batched_count,
                               sample=min(48, args.batched_count))
         elif args.only == "conv":
-            res = conv_leg(dev, tubes=args.surrogate_eval_tubes, patch=args.surrogate_patch,
-                           impl=args.conv_impl)
+            res = conv_leg(dev, tubes=args.surrogate_eval_tubes, impl=args.conv_impl)
         elif args.only == "surrogate":
             res = surrogate_leg(dev, train_tubes=args.surrogate_train_tubes,
                                 eval_tubes=args.surrogate_eval_tubes,

@@ -342,16 +342,16 @@ int lbm_nn_lift(const float *feat, const float *Wl, const float *bl, void *x0, i
 int lbm_nn_lift_backward(const float *gx0, const float *feat, float *gWl, float *gbl, int64_t P,
                          int F, int C, void *stream);
 
-/* Head: out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o] for Fo = 3, 6 or 12 float
- * outputs (patches of 1, 2, 4 nodes); C a multiple of 8, at most 1024; x and
- * Wp 16-byte aligned. */
+/* Head: out[p][o] = sum_c x[p][c] Wp[o][c] + bp[o] for Fo = 3, 6, 12 or 24
+ * float outputs (patches of 1, 2, 4, 8 nodes); C a multiple of 8, at most
+ * 1024; x and Wp 16-byte aligned. */
 int lbm_nn_head(const void *x, const float *Wp, const float *bp, float *out, int64_t P, int C, int Fo,
                 void *stream);
 
 /* Head backward: gx = gout Wp (written), gz = bf16(gx * gelu'(z)) (written;
  * z is the pre-activation of the last conv layer), gWp += gout^T x,
- * gbp += sum_p gout.  C is 128 or 256; Fo is 3, 6 or 12 (patches of 1, 2,
- * 4 nodes). */
+ * gbp += sum_p gout.  C is 128 or 256; Fo is 3, 6, 12 or 24 (patches of 1,
+ * 2, 4, 8 nodes). */
 int lbm_nn_head_backward(const float *gout, const void *x, const float *Wp, const void *z, float *gx,
                          void *gz, float *gWp, float *gbp, int64_t P, int C, int Fo, void *stream);
 

@@ -935,7 +935,8 @@ __global__ void k_head(const __nv_bfloat16 *x, const float *Wp, const float *bp,
 
 // Head backward: gx = gout Wp; gz = bf16(gx gelu'(z)); gWp += gout^T x; gbp += sum gout.
 // One warp per position, lane holding channels lane + 32 j (NJ = C / 32),
-// FO outputs: both compile-time so that the partial sums stay in registers.
+// FO outputs: both compile-time so that the partial sums stay in registers
+// (the head weights are read through L1).
 template <int NJ, int FO>
 __global__ void k_head_bwd(const float *gout, const __nv_bfloat16 *x, const float *Wp,
                            const __nv_bfloat16 *z, float *gx, __nv_bfloat16 *gz, float *gWp,
@@ -944,12 +945,12 @@ __global__ void k_head_bwd(const float *gout, const __nv_bfloat16 *x, const floa
     constexpr int C = 32 * NJ;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    float accW[FO][NJ], accB[FO], wp[FO][NJ];
+    float accW[FO][NJ], accB[FO];
 #pragma unroll
     for (int o = 0; o < FO; ++o) {
         accB[o] = 0.f;
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) accW[o][j] = 0.f, wp[o][j] = __ldg(Wp + o * C + lane + 32 * j);
+        for (int j = 0; j < NJ; ++j) accW[o][j] = 0.f;
     }
     for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
         float go[FO];
@@ -965,7 +966,7 @@ __global__ void k_head_bwd(const float *gout, const __nv_bfloat16 *x, const floa
             float g = 0.f;
 #pragma unroll
             for (int o = 0; o < FO; ++o) {
-                g = fmaf(go[o], wp[o][j], g);
+                g = fmaf(go[o], __ldg(Wp + o * C + lane + 32 * j), g);
                 accW[o][j] = fmaf(go[o], xv, accW[o][j]);
             }
             gx[c] = g;
@@ -1531,7 +1532,7 @@ int lbm_nn_head(const void *x, const float *Wp, const float *bp, float *out, int
                 void *stream)
 {
     if (!x || !Wp || !bp || !out || P < 1 || C < 8 || C > 1024 || C % 8 || !aligned16(x) ||
-        !aligned16(Wp) || (Fo != 3 && Fo != 6 && Fo != 12))
+        !aligned16(Wp) || (Fo != 3 && Fo != 6 && Fo != 12 && Fo != 24))
         return LBM_EINVAL;
     const int64_t nblocks = (P + 127) / 128;
     if (nblocks > 0x7fffffff) return LBM_EINVAL;
@@ -1540,7 +1541,8 @@ int lbm_nn_head(const void *x, const float *Wp, const float *bp, float *out, int
     const size_t sh = sizeof(float) * Fo * C;
     if (Fo == 3) k_head<3><<<(int)nblocks, 128, sh, s>>>(xb, Wp, bp, out, P, C);
     else if (Fo == 6) k_head<6><<<(int)nblocks, 128, sh, s>>>(xb, Wp, bp, out, P, C);
-    else k_head<12><<<(int)nblocks, 128, sh, s>>>(xb, Wp, bp, out, P, C);
+    else if (Fo == 12) k_head<12><<<(int)nblocks, 128, sh, s>>>(xb, Wp, bp, out, P, C);
+    else k_head<24><<<(int)nblocks, 128, sh, s>>>(xb, Wp, bp, out, P, C);
     return launched(cudaGetLastError());
 }
 
@@ -1548,7 +1550,7 @@ int lbm_nn_head_backward(const float *gout, const void *x, const float *Wp, cons
                          void *gz, float *gWp, float *gbp, int64_t P, int C, int Fo, void *stream)
 {
     if (!gout || !x || !Wp || !z || !gx || !gz || !gWp || !gbp || P < 1 ||
-        (C != 128 && C != 256) || (Fo != 3 && Fo != 6 && Fo != 12))
+        (C != 128 && C != 256) || (Fo != 3 && Fo != 6 && Fo != 12 && Fo != 24))
         return LBM_EINVAL;
     const int grid = (int)std::min<int64_t>(grid_for(P * 32), 152 * 4);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1560,11 +1562,13 @@ int lbm_nn_head_backward(const float *gout, const void *x, const float *Wp, cons
     if (C == 128) {
         if (Fo == 3) LBM_HEAD_BWD(4, 3);
         else if (Fo == 6) LBM_HEAD_BWD(4, 6);
-        else LBM_HEAD_BWD(4, 12);
+        else if (Fo == 12) LBM_HEAD_BWD(4, 12);
+        else LBM_HEAD_BWD(4, 24);
     } else {
         if (Fo == 3) LBM_HEAD_BWD(8, 3);
         else if (Fo == 6) LBM_HEAD_BWD(8, 6);
-        else LBM_HEAD_BWD(8, 12);
+        else if (Fo == 12) LBM_HEAD_BWD(8, 12);
+        else LBM_HEAD_BWD(8, 24);
     }
 #undef LBM_HEAD_BWD
     return launched(cudaGetLastError());

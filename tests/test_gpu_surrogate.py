@@ -181,7 +181,7 @@ def oracle_params(arrays, dil, C=128):
                     arrays[2 + 2 * N], arrays[3 + 2 * N], list(dil))
 
 
-@pytest.mark.parametrize("patch,impl", [(1, 0), (2, 0), (1, 1)])
+@pytest.mark.parametrize("patch,impl", [(1, 0), (2, 0), (8, 0), (1, 1)])
 def test_network_output_and_gradients(lbmlib, patch, impl):
     """Loss, output and every gradient block of a 3-layer network against
     the FP64 reference, which rounds to bfloat16 where the kernels do."""
