@@ -15,8 +15,9 @@
 // tensor cores: the Tensor Memory Accelerator copies 128-byte-swizzled tiles
 // straight out of the channel-last tensors (the tap shift is a coordinate
 // offset; rows outside the tube come back as zeros), one thread issues
-// tcgen05.mma into a 128 x 128 fp32 accumulator in tensor memory, and four
-// warps drain it with tcgen05.ld into a fused epilogue.
+// tcgen05.mma into a 128 x 128 fp32 accumulator in tensor memory, and warps
+// drain it with tcgen05.ld into a fused epilogue (4 warps in the
+// one-tile-per-block form, 16 in the persistent form).
 //   forward       D[pos][co] = sum_{t,ci} x[pos+s_t][ci] W[t][co][ci]   (A, B K-major)
 //   input grad    D[pos][ci] = sum_{t,co} gz[pos+s_t][co] WT[t][ci][co] (A, B K-major)
 //   weight grad   D[co][ci]  = sum_pos gz[pos][co] x[pos+s_t][ci]       (A, B MN-major)
@@ -854,14 +855,16 @@ int grid_for(int64_t n, int threads = 256)
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 16));
 }
 
-// x0[p][c] = bf16(sum_j feat[p][j] Wl[c][j] + bl[c]).  Thread c of a block of
-// C threads keeps row c of the weights in registers and walks a range of
-// positions; the F features of a position are one broadcast load per warp
-// (float4s) and the C outputs of a position one coalesced row.
+// x0[p][c] = bf16(sum_j feat[p][j] Wl[c][j] + bl[c]).  A block of C threads
+// takes a range of positions: it first copies their feature rows to shared
+// memory with coalesced 16-byte loads, then thread c (row c of the weights in
+// registers) forms channel c of every position from broadcast reads, so each
+// position's C outputs are one coalesced row.
 template <int F>
 __global__ void k_lift(const float *feat, const float *Wl, const float *bl, __nv_bfloat16 *x0,
                        int64_t P, int C, int64_t per_block)
 {
+    extern __shared__ float4 fsh[];  // [per_block][F / 4]
     const int c = threadIdx.x;
     float w[F];
 #pragma unroll
@@ -871,28 +874,22 @@ __global__ void k_lift(const float *feat, const float *Wl, const float *bl, __nv
     }
     const float bias = bl[c];
     const int64_t p0 = blockIdx.x * per_block, p1 = std::min(P, p0 + per_block);
-    constexpr int G = 4;  // positions whose feature loads are in flight together
-    for (int64_t p = p0; p < p1; p += G) {
-        float4 v[G][F / 4];
+    const int n4 = (int)(p1 - p0) * (F / 4);
+    const float4 *src = reinterpret_cast<const float4 *>(feat + p0 * F);
+    for (int e = c; e < n4; e += blockDim.x) fsh[e] = __ldg(src + e);
+    __syncthreads();
+    for (int64_t p = p0; p < p1; ++p) {
+        const float4 *f = fsh + (p - p0) * (F / 4);
+        float acc = bias;
 #pragma unroll
-        for (int g = 0; g < G; ++g)
-#pragma unroll
-            for (int j = 0; j < F / 4; ++j)
-                v[g][j] = p + g < p1 ? __ldg(reinterpret_cast<const float4 *>(feat + (p + g) * F) + j)
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            if (p + g >= p1) break;
-            float acc = bias;
-#pragma unroll
-            for (int j = 0; j < F / 4; ++j) {
-                acc = fmaf(v[g][j].x, w[4 * j], acc);
-                acc = fmaf(v[g][j].y, w[4 * j + 1], acc);
-                acc = fmaf(v[g][j].z, w[4 * j + 2], acc);
-                acc = fmaf(v[g][j].w, w[4 * j + 3], acc);
-            }
-            x0[(p + g) * C + c] = __float2bfloat16_rn(acc);
+        for (int j = 0; j < F / 4; ++j) {
+            const float4 v = f[j];
+            acc = fmaf(v.x, w[4 * j], acc);
+            acc = fmaf(v.y, w[4 * j + 1], acc);
+            acc = fmaf(v.z, w[4 * j + 2], acc);
+            acc = fmaf(v.w, w[4 * j + 3], acc);
         }
+        x0[p * C + c] = __float2bfloat16_rn(acc);
     }
 }
 
@@ -1159,17 +1156,6 @@ __global__ void k_apply(const float *rho, const float *u, const float *T, const 
     }
 }
 
-__device__ __forceinline__ double block_sum(double v, double *red)
-{
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    return s;
-}
-
 // One block per tube: conservation residual between two states (mass,
 // momentum scaled by mass, total energy with (1+n)/2 T) and, when a
 // reference is given, the L1 error (max over rho, u relative to the sound
@@ -1182,46 +1168,59 @@ __global__ void k_tube_checks(const float *rho, const float *u, const float *T, 
                               const float *gamma, float *residual, float *l1, int *starts, int L,
                               int w0, int W, int span, int margin)
 {
-    __shared__ double red[32];
+    constexpr int NV = 12;
+    __shared__ double red[NV][32];
     __shared__ float best_v[32];
     __shared__ int best_i[32];
     const int b = blockIdx.x;
     const double cv = half_dof ? (double)half_dof[b] : 0.0;  // only read when residual is asked for
-    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double g = l1 ? (double)gamma[b] : 0.0;
+    // totals of the first and second state (mass, momentum, energy), the L1
+    // differences of rho, u, T, and the reference's sound-speed, T and rho sums
+    double s[NV] = {};
     float bv = -1.0f;
     int bi = w0;
     for (int l = w0 + threadIdx.x; l < w0 + W; l += blockDim.x) {
         const int64_t i = (int64_t)b * L + l;
         const double r1 = rho[i], v1 = u[i], t1 = T[i], r2 = rho2[i], v2 = u2[i], t2 = T2[i];
-        s[0] += r1;
-        s[1] += r1 * v1;
-        s[2] += r1 * (cv * t1 + 0.5 * v1 * v1);
-        s[3] += r2;
-        s[4] += r2 * v2;
-        s[5] += r2 * (cv * t2 + 0.5 * v2 * v2);
-        s[6] += fabs(r1 - r2);
-        s[7] += fabs(v1 - v2);
-        s[8] += fabs(t1 - t2);
+        if (residual) {
+            s[0] += r1;
+            s[1] += r1 * v1;
+            s[2] += r1 * (cv * t1 + 0.5 * v1 * v1);
+            s[3] += r2;
+            s[4] += r2 * v2;
+            s[5] += r2 * (cv * t2 + 0.5 * v2 * v2);
+        }
+        if (l1) {
+            s[6] += fabs(r1 - r2);
+            s[7] += fabs(v1 - v2);
+            s[8] += fabs(t1 - t2);
+            s[9] += sqrt(g * t2);
+            s[10] += fabs(t2);
+            s[11] += fabs(r2);
+        }
         const float d = fabsf(rho2[i] - rho[i]);
         if (!(d <= bv)) {  // also takes a non-finite change
             bv = isfinite(d) ? d : INFINITY;
             bi = l;
         }
     }
-    double tot[9];
-    for (int q = 0; q < 9; ++q) tot[q] = block_sum(s[q], red);
-    // sound-speed and temperature sums of the reference (second) state
-    double cs = 0.0, ts = 0.0;
-    if (l1) {
-        const double g = gamma[b];
-        for (int l = w0 + threadIdx.x; l < w0 + W; l += blockDim.x) {
-            const int64_t i = (int64_t)b * L + l;
-            cs += sqrt(g * (double)T2[i]);
-            ts += fabs((double)T2[i]);
-        }
-        cs = block_sum(cs, red);
-        ts = block_sum(ts, red);
+    // one block-wide reduction of all the sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double v = s[q];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[q][warp] = v;
     }
+    __syncthreads();
+    double tot[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        tot[q] = 0.0;
+        for (int w = 0; w < nw; ++w) tot[q] += red[q][w];
+    }
+    const double cs = tot[9], ts = tot[10];
     if (starts) {  // argmax of |rho2 - rho|, smallest index on ties
         for (int off = 16; off > 0; off >>= 1) {
             const float ov = __shfl_down_sync(0xffffffffu, bv, off);
@@ -1246,7 +1245,7 @@ __global__ void k_tube_checks(const float *rho, const float *u, const float *T, 
             residual[b] = (float)fmax(m, fmax(j, e));
         }
         if (l1) {
-            const double er = tot[6] / fabs(tot[3]);
+            const double er = tot[6] / tot[11];
             const double eu = tot[7] / cs;
             const double et = tot[8] / ts;
             l1[b] = (float)fmax(er, fmax(eu, et));
@@ -1495,17 +1494,18 @@ int lbm_nn_lift(const float *feat, const float *Wl, const float *bl, void *x0, i
     if (!feat || !Wl || !bl || !x0 || P < 1 || C < 32 || C > 1024 || C % 32 ||
         (F != 4 && F != 8 && F != 16 && F != 32) || !aligned16(feat) || !aligned16(Wl))
         return LBM_EINVAL;
-    const int64_t per_block = 256;
+    const int64_t per_block = 256;  // feature rows staged per block: 4 KB to 32 KB
     const int64_t nblocks = (P + per_block - 1) / per_block;
     if (nblocks > 0x7fffffff) return LBM_EINVAL;
     const int blocks = (int)nblocks;
+    const size_t sh = (size_t)per_block * F * sizeof(float);
     cudaStream_t s = (cudaStream_t)stream;
     auto out = (__nv_bfloat16 *)x0;
     switch (F) {
-    case 4: k_lift<4><<<blocks, C, 0, s>>>(feat, Wl, bl, out, P, C, per_block); break;
-    case 8: k_lift<8><<<blocks, C, 0, s>>>(feat, Wl, bl, out, P, C, per_block); break;
-    case 16: k_lift<16><<<blocks, C, 0, s>>>(feat, Wl, bl, out, P, C, per_block); break;
-    default: k_lift<32><<<blocks, C, 0, s>>>(feat, Wl, bl, out, P, C, per_block); break;
+    case 4: k_lift<4><<<blocks, C, sh, s>>>(feat, Wl, bl, out, P, C, per_block); break;
+    case 8: k_lift<8><<<blocks, C, sh, s>>>(feat, Wl, bl, out, P, C, per_block); break;
+    case 16: k_lift<16><<<blocks, C, sh, s>>>(feat, Wl, bl, out, P, C, per_block); break;
+    default: k_lift<32><<<blocks, C, sh, s>>>(feat, Wl, bl, out, P, C, per_block); break;
     }
     return launched(cudaGetLastError());
 }

@@ -44,8 +44,9 @@ class ConvOperator:
 
     ``patch`` consecutive nodes form one position of the network (4 patch
     features in, 3 patch outputs), so the body runs on L / patch positions.
-    ``impl`` 0 runs the convolutions on the tensor cores (tcgen05), 1 on the
-    CUDA cores.
+    ``impl`` 0 runs the convolutions on the tensor cores (tcgen05, persistent
+    kernels), 2 on the tensor cores one output tile per block, 1 on the CUDA
+    cores.
     """
 
     def __init__(self, C=128, k=5, dilations=DEFAULT_DILATIONS, patch=1, seed=0, device=None,
