@@ -16,8 +16,15 @@ namespace {
 
 constexpr int kQ343 = 343;
 
+// Resident blocks per SM the register allocation must allow.  Left free the
+// compiler takes 185-207 registers (2 blocks of 4 warps); 3 blocks (at most
+// 170 registers, 0-20 bytes of spill) measured 13 % (n = 0) and 7 % (n = 4) faster on
+// the 384^3 f16 blast, 4 and 5 blocks spill and are slower.
+#ifndef LBM_Q343_MIN_BLOCKS
+#define LBM_Q343_MIN_BLOCKS 3
+#endif
 template <bool ROT, typename ST>
-__global__ void __launch_bounds__(kBlockX) k_step_q343(const Params<kQ343, ST> p)
+__global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(const Params<kQ343, ST> p)
 {
     constexpr int D = 3;
     constexpr int C = (kQ343 - 1) / 2;  // rest velocity (171)
