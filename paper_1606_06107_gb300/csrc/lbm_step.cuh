@@ -28,17 +28,21 @@ namespace lbm {
 constexpr int kBlockX = 128;
 
 // Minimum resident blocks per SM requested from the compiler for the step
-// kernel (0: no request, the compiler's own choice).  4 caps the D2Q49
-// kernel at 128 registers without spills; measured 4 % faster than letting
-// the compiler choose and 4-13 % faster than 3 or 5 on the 2048^2 workload.
-#ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 4
-#endif
-#if LBM_STEP_MIN_BLOCKS > 0
-#define LBM_STEP_BOUNDS __launch_bounds__(kBlockX, LBM_STEP_MIN_BLOCKS)
+// kernel, by storage type.  float: 4 caps the D2Q49 kernel at 128 registers
+// without spills; measured 4 % faster than letting the compiler choose and
+// 4-13 % faster than 3 or 5 on the 2048^2 workload.  half/bfloat16
+// deviations in STREAM mode (more instructions per population, half the
+// bytes): 5 blocks measured 9 % (f16) and 13 % (bf16) faster than 4 on the
+// same workload, 3 slower, 6 no better; FD mode keeps 4 (at 5 its rotational
+// variant spills 256 bytes).  LBM_STEP_MIN_BLOCKS overrides all (A/B builds).
+template <typename ST, int MODE> struct StepMinBlocks {
+#ifdef LBM_STEP_MIN_BLOCKS
+    static constexpr int value = LBM_STEP_MIN_BLOCKS;
 #else
-#define LBM_STEP_BOUNDS __launch_bounds__(kBlockX)
+    static constexpr int value = (std::is_same<ST, float>::value || MODE != 0) ? 4 : 5;
 #endif
+};
+#define LBM_STEP_BOUNDS __launch_bounds__(kBlockX, StepMinBlocks<ST, MODE>::value)
 
 // ---------------------------------------------------------------------------
 // Velocity sets.  xi_i = r * e_i; order (ez, ey, ex) ascending.  The sets are
