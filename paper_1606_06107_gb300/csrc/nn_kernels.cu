@@ -59,12 +59,14 @@ __device__ __forceinline__ float tanh_fast(float x)
     return y;
 }
 
-// GELU in its tanh form and its derivative.
+// GELU in its tanh form, x/2 (1 + tanh(c (x + 0.044715 x^3))), written as
+// fma(x/2, tanh(u), x/2) with u = x (c + 0.044715 c x^2), and its derivative.
 __device__ __forceinline__ float gelu(float x)
 {
     const float c = 0.7978845608028654f;  // sqrt(2/pi)
-    const float th = tanh_fast(c * fmaf(0.044715f * x, x * x, x));
-    return 0.5f * x * (1.0f + th);
+    const float th = tanh_fast(x * fmaf(x * x, 0.044715f * c, c));
+    const float h = 0.5f * x;
+    return fmaf(h, th, h);
 }
 
 __device__ __forceinline__ float gelu_grad(float x)
