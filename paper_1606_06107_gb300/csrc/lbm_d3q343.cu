@@ -5,7 +5,10 @@
 // populations twice: a first pass accumulates rho, j and sum |e|^2 g (row
 // sums by (e_y, e_z), column sums by e_x), a second pass re-reads each value
 // (from L1/L2: a 128-node block touches 343 x 128 x 4 B = 175 KB between the
-// two reads) and writes its post-collision value.  The rest and the six unit
+// two reads) and writes its post-collision value.  The second pass walks the
+// e_z planes in reverse, so that it starts on the lines the first pass loaded
+// last, which are the ones still in L1 (7 % faster with float storage, 1 %
+// with f16).  The rest and the six unit
 // velocities are stored last with the float32 moment corrections, as in the
 // one- and two-dimensional kernels.  Element indices are 64-bit (the state
 // of a 384^3 grid holds 2 x 10^10 values).
@@ -87,7 +90,8 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
     float g_c = 0.f, g_mx = 0.f, g_px = 0.f, g_my = 0.f, g_py = 0.f, g_mz = 0.f, g_pz = 0.f;
     // The correction sums are accumulated per row of 7 and then per plane, so
     // each carries the rounding of ~2 x 7 additions rather than of 343.
-    for (int c = 0; c < 7; ++c) {
+    // Planes in reverse order (see above).
+    for (int c = 6; c >= 0; --c) {
         const int zo = bc_wrap(z - (c - 3), p.Z, p.bc2) * plane;
         const int ez = c - 3;
         float p0 = 0.f, p2 = 0.f, px = 0.f, py = 0.f;  // plane sums
