@@ -285,8 +285,9 @@ def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int =
     y = torch.empty_like(x)
     from paper_1606_06107_gb300.surrogate import _fp
     conv = lambda: net.lib.lbm_nn_conv_forward(_fp(x), net._wb(0), net._ptr(net.params, "b", 0),
-                                               _fp(y), None, eval_tubes, Lp, C, net.k, 2, 0,
-                                               _fp(net.status), stream.cuda_stream)
+                                               _fp(y), None, eval_tubes, Lp, C, net.k, 2,
+                                               net.conv_impl(2), _fp(net.status),
+                                               stream.cuda_stream)
     for _ in range(3):
         conv()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -416,12 +417,14 @@ def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int =
             "network": {"params": net.n_params, "channels": C, "taps": net.k,
                         "layers": net.N, "dilations": list(net.dil), "patch": patch,
                         "dtype": "bf16 weights/activations, fp32 accumulation"},
-            "roofline": {"bound": "tensor", "kernel": "k_conv_tcp<forward>",
+            "roofline": {"bound": "tensor",
+                         "kernel": "k_conv_tcn<forward>" if net.conv_impl(2) == 3 else
+                                   "k_conv_tcp<forward>",
                          "achieved": conv_tflops, "unit": "TFLOP/s", "avg_launch_ms": conv_ms}}
 
 
 def conv_leg(dev, tubes: int = 1024, L: int = 4096, patch: int = 4, C: int = 128, k: int = 5,
-             dil: int = 2, reps: int = 20, impl: int = 0):
+             dil: int = 2, reps: int = 20, impl: int = 3):
     """The surrogate's three tensor-core convolution products alone, at the
     inference shape (tubes x L/patch positions x C channels): forward with
     the fused GELU/residual epilogue, input gradient with the fused
@@ -769,7 +772,7 @@ def main():
     ap.add_argument("--surrogate-windows", type=int, default=125)
     ap.add_argument("--surrogate-seconds", type=float, default=60.0)
     ap.add_argument("--surrogate-patch", type=int, default=4)
-    ap.add_argument("--conv-impl", type=int, default=0,
+    ap.add_argument("--conv-impl", type=int, default=3,
                     help="convolution kernel for --only conv (include/lbm.h impl codes)")
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--batched-steps", type=int, default=4000)

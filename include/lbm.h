@@ -297,8 +297,12 @@ void lbm_batch_destroy(lbm_batch b);
  * multiple of 128, gradients of the residual stream float32 in the same
  * layout, conv weights bfloat16 [k][C][C].  `impl` selects the tensor-core
  * kernels (0: tcgen05 MMA fed by the Tensor Memory Accelerator, operands
- * 16-byte aligned, persistent blocks; 2: the same, one output tile per
- * block) or the CUDA-core ones (1).  `status` (device int, may be
+ * 16-byte aligned, persistent blocks, 128 positions x 128 channels per
+ * tile; 3: the same with 128 channels x 256 positions per tile and one
+ * activation window per 64-channel chunk read by all taps, for
+ * (k - 1) dil <= 64, else LBM_EINVAL; 2: one output tile per block) or the
+ * CUDA-core ones (1); the weight gradient runs the same kernel for 0, 2
+ * and 3.  `status` (device int, may be
  * NULL) receives bit 4 if a tensor-core kernel gave up waiting on a
  * barrier, in which case its outputs are not written.  Calls are
  * asynchronous on `stream`; they return LBM_OK, LBM_EINVAL (bad pointer,

@@ -23,8 +23,10 @@
 //   weight grad   D[co][ci]  = sum_pos gz[pos][co] x[pos+s_t][ci]       (A, B MN-major)
 // The forward and input-gradient products run persistent (impl 0: one block
 // per SM, double-buffered accumulators so that the epilogue of a tile
-// overlaps the MMAs of the next) or one tile per block (impl 2); a
-// CUDA-core implementation of all three (impl 1) is the comparison point.
+// overlaps the MMAs of the next; impl 3: the same with channels x 256
+// positions per tile and one activation window per channel chunk shared by
+// the taps) or one tile per block (impl 2); a CUDA-core implementation of
+// all three (impl 1) is the comparison point.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -440,10 +442,14 @@ constexpr int kPSmemBytes = kPStages * kStageBytes + kStagingBytes + 1024 + 256;
 // global load and store is done cooperatively: COLS/4 lanes cover the COLS
 // columns of one row, so each instruction touches whole row segments.
 template <int EPI, int COLS = 64>
+__device__ __forceinline__ void finish_rows(const ConvArgs &a, const float *st, int b, int l_first,
+                                            int n0, bool skip);
+
+template <int EPI, int COLS = 64>
 __device__ __forceinline__ void epilogue_rows(const ConvArgs &a, float *st, uint32_t taddr, int b,
                                               int l_first, int n0, bool skip)
 {
-    constexpr int kPitch = COLS + 4, kLpr = COLS / 4, kRpi = 32 / kLpr, kBatch = 4;
+    constexpr int kPitch = COLS + 4;
     const int lane = threadIdx.x & 31;
 #pragma unroll 1
     for (int c = 0; c < COLS; c += 32) {
@@ -456,6 +462,19 @@ __device__ __forceinline__ void epilogue_rows(const ConvArgs &a, float *st, uint
                 make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
     }
     __syncwarp();
+    finish_rows<EPI, COLS>(a, st, b, l_first, n0, skip);
+}
+
+// Second half of the epilogue: the staged block (32 rows = positions
+// l_first.., COLS channels n0.., pitch COLS + 4 floats) is read back so
+// that COLS/4 lanes cover the COLS channels of one row and every global
+// load and store touches whole row segments.
+template <int EPI, int COLS>
+__device__ __forceinline__ void finish_rows(const ConvArgs &a, const float *st, int b, int l_first,
+                                            int n0, bool skip)
+{
+    constexpr int kPitch = COLS + 4, kLpr = COLS / 4, kRpi = 32 / kLpr, kBatch = 4;
+    const int lane = threadIdx.x & 31;
     if (!skip) {
         const int cg = (lane % kLpr) * 4;
         float4 bias = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -651,6 +670,210 @@ __global__ void __launch_bounds__(kPThreads, 1)
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTile)
+                     : "memory");
+    }
+}
+
+// Persistent form with the roles of the operands exchanged (impl 3): the
+// output channels are the MMA's M = 128 rows (A = the weight tile, K-major)
+// and 256 positions its N columns (B = activations, K-major), so one
+// tcgen05.mma of 128 x 256 x 16 reads 12 KB of operands from shared memory
+// instead of 16 KB for the same work as two 128 x 128 x 16 ones.  For each
+// 64-channel chunk one window of 256 + (k-1) dil positions is loaded once
+// and the k taps read it at row offsets t dil (sub-window descriptors),
+// instead of one shifted tile per tap; the weight tiles stream through a
+// 4-stage ring.  Two 256-column accumulators fill the 512 columns of tensor
+// memory.  After tcgen05.ld a lane holds one channel at 32 positions; the
+// staging store writes it transposed, so the read-back and the global I/O
+// are those of the other persistent form.
+constexpr int kNPos = 256;                         // positions per tile (MMA N)
+constexpr int kXStages = 2;                        // activation windows in flight
+constexpr int kWStages = 4;                        // weight tiles in flight
+constexpr int kWTileBytes = kTile * kChunk * 2;    // 128 channels x 64 input channels
+constexpr int kMaxHalo = 64;                       // largest (k-1) dil a window holds
+constexpr int kNSmemFixed = kWStages * kWTileBytes + kStagingBytes + 1024 + 256;
+
+// Window rows: 256 + (k-1) dil rounded up to 16, loaded as two boxes of
+// half that (each a multiple of 8 rows, so both halves start 1024-byte aligned).
+__host__ __device__ constexpr int window_rows(int k, int dil)
+{
+    return kNPos + ((k - 1) * dil + 15) / 16 * 16;
+}
+__host__ __device__ constexpr int tcn_smem_bytes(int rows) { return kNSmemFixed + kXStages * rows * 128; }
+constexpr int kNSmemMax = kNSmemFixed + kXStages * (kNPos + kMaxHalo) * 128;
+static_assert(kNSmemMax <= 227 * 1024, "shared memory of the transposed persistent form");
+static_assert((kNPos + kMaxHalo) / 2 <= 256, "TMA box rows");
+
+// Instruction descriptor of kind::f16 with fp32 accumulation, bf16 operands,
+// M x N, both operands K-major.
+__host__ __device__ constexpr uint32_t instr_desc_mn(uint32_t m, uint32_t n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kPThreads, 1)
+    k_conv_tcn(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
+               ConvArgs a, int tiles_l, int tiles_m, int total, int rows)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *wbuf = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *xbuf = wbuf + kWStages * kWTileBytes;
+    const int xbytes = rows * 128;
+    float *staging = (float *)(xbuf + kXStages * xbytes);
+    uint64_t *wfull = (uint64_t *)((uint8_t *)staging + kStagingBytes);
+    uint64_t *wempty = wfull + kWStages;
+    uint64_t *xfull = wempty + kWStages;
+    uint64_t *xempty = xfull + kXStages;
+    uint64_t *tfull = xempty + kXStages;   // accumulator a ready for the epilogue
+    uint64_t *tempty = tfull + 2;          // accumulator a drained by the epilogue
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
+    __shared__ volatile int failed;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kWStages; ++i) {
+            mbar_init(&wfull[i], 1);
+            mbar_init(&wempty[i], 1);
+        }
+        for (int i = 0; i < kXStages; ++i) {
+            mbar_init(&xfull[i], 1);
+            mbar_init(&xempty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], kEpiWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
+    __syncwarp();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(saddr(tmem_slot)), "r"(2 * kNPos) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int chunks = a.C / kChunk;
+    const int halo = (a.k / 2) * a.dil;  // window row 0 is position l0 - halo
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            int gx = 0, gw = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+                const int co0 = (tile % tiles_m) * kTile, rest = tile / tiles_m;
+                const int b = rest / tiles_l, l0 = (rest % tiles_l) * kNPos;
+                for (int ch = 0; ch < chunks && ok; ++ch, ++gx) {
+                    const int xs = gx % kXStages, xuse = gx / kXStages;
+                    if (xuse > 0 && !mbar_wait(&xempty[xs], (xuse - 1) & 1, a.status)) {
+                        failed = 1;
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *win = xbuf + xs * xbytes;
+                    mbar_expect_tx(&xfull[xs], xbytes);
+                    tma_load_3d(win, &map_x, &xfull[xs], ch * kChunk, l0 - halo, b);
+                    tma_load_3d(win + xbytes / 2, &map_x, &xfull[xs], ch * kChunk,
+                                l0 - halo + rows / 2, b);
+                    for (int t = 0; t < a.k; ++t, ++gw) {
+                        const int ws = gw % kWStages, wuse = gw / kWStages;
+                        if (wuse > 0 && !mbar_wait(&wempty[ws], (wuse - 1) & 1, a.status)) {
+                            failed = 1;
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&wfull[ws], kWTileBytes);
+                        tma_load_2d(wbuf + ws * kWTileBytes, &map_w, &wfull[ws], ch * kChunk,
+                                    t * a.C + co0);
+                    }
+                }
+            }
+            // wait (bounded) for the last loads so that none lands after exit
+            for (int q = std::max(0, gx - kXStages); q < gx; ++q)
+                mbar_wait(&xfull[q % kXStages], (q / kXStages) & 1, a.status);
+            for (int q = std::max(0, gw - kWStages); q < gw; ++q)
+                mbar_wait(&wfull[q % kWStages], (q / kWStages) & 1, a.status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            constexpr uint32_t idesc = instr_desc_mn(kTile, kNPos);
+            int gx = 0, gw = 0, it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x, ++it) {
+                const int acc = it & 1, use = it >> 1;
+                const uint32_t d = tmem + acc * kNPos;
+                if (use > 0 && !mbar_wait(&tempty[acc], (use - 1) & 1, a.status)) {
+                    failed = 1;
+                    break;
+                }
+                tc_fence_after();
+                for (int ch = 0; ch < chunks && ok; ++ch, ++gx) {
+                    const int xs = gx % kXStages;
+                    if (!mbar_wait(&xfull[xs], (gx / kXStages) & 1, a.status)) {
+                        failed = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t xt = saddr(xbuf + xs * xbytes);
+                    for (int t = 0; t < a.k; ++t, ++gw) {
+                        const int ws = gw % kWStages;
+                        if (!mbar_wait(&wfull[ws], (gw / kWStages) & 1, a.status)) {
+                            failed = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t wt = saddr(wbuf + ws * kWTileBytes);
+                        const uint32_t bt = xt + (uint32_t)(t * a.dil) * 128u;
+#pragma unroll
+                        for (int kk = 0; kk < kChunk / 16; ++kk)
+                            mma_bf16(d, smem_desc(wt + kk * 32, 16, 1024),
+                                     smem_desc(bt + kk * 32, 16, 1024), idesc, (ch | t | kk) != 0);
+                        mma_commit(&wempty[ws]);
+                    }
+                    mma_commit(&xempty[xs]);
+                }
+                mma_commit(&tfull[acc]);
+            }
+        }
+    } else {  // epilogue warps: lane quarter warp % 4 (32 channels), 64 positions each
+        const int e = warp - 2, quarter = warp & 3, pos0 = (e >> 2) * 64;
+        float *st = staging + e * 32 * kStagePitch;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
+            const int acc = it & 1, use = it >> 1;
+            const int co0 = (tile % tiles_m) * kTile, rest = tile / tiles_m;
+            const int b = rest / tiles_l, l0 = (rest % tiles_l) * kNPos;
+            bool ready = mbar_wait(&tfull[acc], use & 1, a.status);
+            __syncwarp();
+            if (!ready) failed = 1;
+            tc_fence_after();
+#pragma unroll 1
+            for (int h = 0; h < 64; h += 32) {
+                float v[32];
+                __syncwarp();
+                tmem_ld32(tmem + acc * kNPos + ((uint32_t)(quarter * 32) << 16) + pos0 + h, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) st[j * kStagePitch + lane] = v[j];
+                __syncwarp();
+                finish_rows<EPI, 32>(a, st, b, l0 + pos0 + h, co0 + quarter * 32, failed != 0);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&tempty[acc]))
+                                        : "memory");
+            if (failed) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kNPos)
                      : "memory");
     }
 }
@@ -1343,7 +1566,11 @@ int set_smem_attrs()
         cudaFuncSetAttribute(k_conv_tcp<kEpiForward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kPSmemBytes) != cudaSuccess ||
         cudaFuncSetAttribute(k_conv_tcp<kEpiInputGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kPSmemBytes) != cudaSuccess)
+                             kPSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_tcn<kEpiForward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kNSmemMax) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_tcn<kEpiInputGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kNSmemMax) != cudaSuccess)
         return LBM_ECUDA;
     done[dev] = true;
     return LBM_OK;
@@ -1357,6 +1584,7 @@ bool conv_shape_ok(int B, int L, int C, int k, int dil, int impl)
         return false;
     if ((int64_t)(k / 2) * dil >= (1 << 20) || (int64_t)B * L * C >= (1ll << 40)) return false;
     if (impl == 1) return k <= kSimtMaxK && (k - 1) * dil <= kSimtMaxSpan - kSimtTX;
+    if (impl == 3) return (int64_t)(k - 1) * dil <= kMaxHalo && (int64_t)k * C <= (1 << 20);
     return (impl == 0 || impl == 2) && (int64_t)k * C <= (1 << 20);
 }
 
@@ -1395,6 +1623,23 @@ int conv_common(int epi, const void *in, const void *w, const ConvArgs &a, int i
     int rc = set_smem_attrs();
     if (rc != LBM_OK) return rc;
     CUtensorMap ma, mw;
+    if (impl == 3) {  // persistent, channels x 256 positions per tile
+        const int rows = window_rows(a.k, a.dil);
+        if (!map_act(&ma, in, a.B, a.L, a.C, rows / 2) || !map_w(&mw, w, a.C, a.k)) return LBM_ECUDA;
+        const int tiles_l = (a.L + kNPos - 1) / kNPos, tiles_m = a.C / kTile;
+        const int64_t total = (int64_t)tiles_l * tiles_m * a.B;
+        const int sms = sm_count();
+        if (sms < 1 || total >= (1ll << 31)) return LBM_ECUDA;
+        const int grid = (int)std::min<int64_t>(total, sms);
+        const int smem = tcn_smem_bytes(rows);
+        if (epi == kEpiForward)
+            k_conv_tcn<kEpiForward><<<grid, kPThreads, smem, s>>>(ma, mw, a, tiles_l, tiles_m,
+                                                                  (int)total, rows);
+        else
+            k_conv_tcn<kEpiInputGrad><<<grid, kPThreads, smem, s>>>(ma, mw, a, tiles_l, tiles_m,
+                                                                    (int)total, rows);
+        return launched(cudaGetLastError());
+    }
     if (!map_act(&ma, in, a.B, a.L, a.C, kTile) || !map_w(&mw, w, a.C, a.k)) return LBM_ECUDA;
     const int tiles_l = (a.L + kTile - 1) / kTile, tiles_n = a.C / kTile;
     if (impl == 2) {  // one output tile per block

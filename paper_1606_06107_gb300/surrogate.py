@@ -44,13 +44,15 @@ class ConvOperator:
 
     ``patch`` consecutive nodes form one position of the network (4 patch
     features in, 3 patch outputs), so the body runs on L / patch positions.
-    ``impl`` 0 runs the convolutions on the tensor cores (tcgen05, persistent
-    kernels), 2 on the tensor cores one output tile per block, 1 on the CUDA
-    cores.
+    ``impl`` 3 runs the convolutions on the tensor cores (tcgen05, persistent,
+    128 channels x 256 positions per tile; layers whose halo (k - 1) d
+    exceeds 64 positions take impl 0), 0 on the persistent tensor-core form
+    with 128 x 128 tiles, 2 on the tensor cores one output tile per block, 1
+    on the CUDA cores.
     """
 
     def __init__(self, C=128, k=5, dilations=DEFAULT_DILATIONS, patch=1, seed=0, device=None,
-                 impl=0, in_scale=(1.0, 1.0, 1.0, 0.25), out_scale=(1.0, 1.0, 1.0)):
+                 impl=3, in_scale=(1.0, 1.0, 1.0, 0.25), out_scale=(1.0, 1.0, 1.0)):
         import torch
 
         self.torch = torch
@@ -185,13 +187,20 @@ class ConvOperator:
             z = bufs["z"][i] if train else None
             self._check(lib.lbm_nn_conv_forward(_fp(src), self._wb(i), self._ptr(self.params, "b", i),
                                                 _fp(dst), _fp(z), B, Lp, self.C, self.k, d,
-                                                self.impl, _fp(self.status), s),
+                                                self.conv_impl(d), _fp(self.status), s),
                         "lbm_nn_conv_forward")
         last = x[self.N] if train else x[self.N % 2]
         self._check(lib.lbm_nn_head(_fp(last), self._ptr(self.params, "Wp"),
                                     self._ptr(self.params, "bp"), _fp(bufs["out"]), P, self.C,
                                     self.Fo, s), "lbm_nn_head")
         return bufs["out"]
+
+    def conv_impl(self, d):
+        """Kernel code for a layer of dilation d (impl 3 holds a halo of
+        (k - 1) d <= 64 positions per window)."""
+        if self.impl == 3 and (self.k - 1) * d > 64:
+            return 0
+        return self.impl
 
     def backward(self, feat, gout, B, L):
         """Gradients of the loss with d loss / d out = gout into self.grads
@@ -214,13 +223,13 @@ class ConvOperator:
             self._check(lib.lbm_nn_bias_grad(_fp(gz[cur]), self._ptr(g, "b", i), P, self.C, s),
                         "lbm_nn_bias_grad")
             self._check(lib.lbm_nn_conv_backward_weight(_fp(gz[cur]), _fp(x[i]), self._ptr(g, "W", i),
-                                                        B, Lp, self.C, self.k, d, self.impl,
-                                                        _fp(self.status), s),
+                                                        B, Lp, self.C, self.k, d,
+                                                        self.conv_impl(d), _fp(self.status), s),
                         "lbm_nn_conv_backward_weight")
             zp, gzp = (z[i - 1], gz[1 - cur]) if i > 0 else (None, None)
             self._check(lib.lbm_nn_conv_backward_data(_fp(gz[cur]), self._wt(i), _fp(gx), _fp(zp),
                                                       _fp(gzp), B, Lp, self.C, self.k, d,
-                                                      self.impl, _fp(self.status), s),
+                                                      self.conv_impl(d), _fp(self.status), s),
                         "lbm_nn_conv_backward_data")
             cur = 1 - cur
         self._check(lib.lbm_nn_lift_backward(_fp(gx), _fp(feat), self._ptr(g, "Wl"),

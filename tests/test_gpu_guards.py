@@ -148,7 +148,7 @@ def test_ensemble_writes_only_its_buffers(lbmlib):
         lib.lbm_batch_destroy(h)
 
 
-@pytest.mark.parametrize("impl", [0, 1, 2])
+@pytest.mark.parametrize("impl", [0, 1, 2, 3])
 def test_convolutions_write_only_their_buffers(lbmlib, impl):
     """Ragged tube length (77 positions: a 128-row tile and a 64-row weight
     block both reach past it) and three tubes."""

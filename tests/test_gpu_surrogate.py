@@ -58,11 +58,12 @@ CONV_CASES = [  # (B, L, C, k, dil)
     (3, 300, 128, 5, 3),
     (2, 128, 128, 5, 1),
     (1, 77, 256, 3, 2),
+    (96, 1000, 128, 5, 4),   # several tiles per persistent block, ragged tube ends
     (2, 515, 128, 7, 4),
 ]
 
 
-@pytest.mark.parametrize("impl", [0, 1, 2])
+@pytest.mark.parametrize("impl", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", CONV_CASES)
 def test_conv_forward(lbmlib, impl, case):
     B, L, C, k, d = case
@@ -90,7 +91,7 @@ def test_conv_forward(lbmlib, impl, case):
         erry.max()
 
 
-@pytest.mark.parametrize("impl", [0, 1, 2])
+@pytest.mark.parametrize("impl", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", CONV_CASES)
 def test_conv_backward_data(lbmlib, impl, case):
     B, L, C, k, d = case
@@ -158,7 +159,9 @@ def test_conv_rejects_bad_arguments(lbmlib):
     assert ok(vp(x), vp(w), vp(b), vp(y), None, 2, 64, 96, 5, 1, 0, None, s) == -1   # C % 128
     assert ok(vp(x), vp(w), vp(b), vp(y), None, 2, 64, 128, 4, 1, 0, None, s) == -1  # even k
     assert ok(vp(x), vp(w), vp(b), vp(x), None, 2, 64, 128, 5, 1, 0, None, s) == -1  # x == y
-    assert ok(vp(x), vp(w), vp(b), vp(y), None, 2, 64, 128, 5, 1, 3, None, s) == -1  # impl
+    assert ok(vp(x), vp(w), vp(b), vp(y), None, 2, 64, 128, 5, 1, 4, None, s) == -1  # impl
+    # impl 3 holds a halo of (k - 1) dil <= 64 positions in its window
+    assert ok(vp(x), vp(w), vp(b), vp(y), None, 2, 64, 128, 5, 17, 3, None, s) == -1
     off = ctypes.c_void_p(x.data_ptr() + 2)                                         # alignment
     assert ok(off, vp(w), vp(b), vp(y), None, 1, 64, 128, 5, 1, 0, None, s) == -1
 
@@ -181,7 +184,7 @@ def oracle_params(arrays, dil, C=128):
                     arrays[2 + 2 * N], arrays[3 + 2 * N], list(dil))
 
 
-@pytest.mark.parametrize("patch,impl", [(1, 0), (2, 0), (8, 0), (1, 1)])
+@pytest.mark.parametrize("patch,impl", [(1, 3), (2, 3), (8, 3), (1, 0), (1, 1)])
 def test_network_output_and_gradients(lbmlib, patch, impl):
     """Loss, output and every gradient block of a 3-layer network against
     the FP64 reference, which rounds to bfloat16 where the kernels do."""
