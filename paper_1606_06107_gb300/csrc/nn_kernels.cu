@@ -1398,33 +1398,39 @@ __global__ void k_tube_checks(const float *rho, const float *u, const float *T, 
     __shared__ float best_v[32];
     __shared__ int best_i[32];
     const int b = blockIdx.x;
-    const double cv = half_dof ? (double)half_dof[b] : 0.0;  // only read when residual is asked for
-    const double g = l1 ? (double)gamma[b] : 0.0;
-    // totals of the first and second state (mass, momentum, energy), the L1
-    // differences of rho, u, T, and the reference's sound-speed, T and rho sums
-    double s[NV] = {};
+    const float cv = half_dof ? half_dof[b] : 0.f;  // only read when residual is asked for
+    const float g = l1 ? gamma[b] : 0.f;
+    // Per node in float, per thread in float (a few tens of terms), across
+    // the block in double.  The residual sums accumulate the differences
+    // of the two states node by node, so a small change keeps its digits:
+    // totals of the first state (mass, momentum, energy), their changes,
+    // the L1 differences of rho, u, T and the reference's sound-speed, T
+    // and rho sums.
+    float s[NV] = {};
     float bv = -1.0f;
     int bi = w0;
     for (int l = w0 + threadIdx.x; l < w0 + W; l += blockDim.x) {
         const int64_t i = (int64_t)b * L + l;
-        const double r1 = rho[i], v1 = u[i], t1 = T[i], r2 = rho2[i], v2 = u2[i], t2 = T2[i];
+        const float r1 = rho[i], v1 = u[i], t1 = T[i], r2 = rho2[i], v2 = u2[i], t2 = T2[i];
         if (residual) {
+            const float j1 = r1 * v1;
+            const float e1 = r1 * fmaf(cv, t1, 0.5f * v1 * v1);
             s[0] += r1;
-            s[1] += r1 * v1;
-            s[2] += r1 * (cv * t1 + 0.5 * v1 * v1);
-            s[3] += r2;
-            s[4] += r2 * v2;
-            s[5] += r2 * (cv * t2 + 0.5 * v2 * v2);
+            s[1] += j1;
+            s[2] += e1;
+            s[3] += r2 - r1;
+            s[4] += fmaf(r2, v2, -j1);
+            s[5] += fmaf(r2, fmaf(cv, t2, 0.5f * v2 * v2), -e1);
         }
         if (l1) {
-            s[6] += fabs(r1 - r2);
-            s[7] += fabs(v1 - v2);
-            s[8] += fabs(t1 - t2);
-            s[9] += sqrt(g * t2);
-            s[10] += fabs(t2);
-            s[11] += fabs(r2);
+            s[6] += fabsf(r1 - r2);
+            s[7] += fabsf(v1 - v2);
+            s[8] += fabsf(t1 - t2);
+            s[9] += sqrtf(g * t2);
+            s[10] += fabsf(t2);
+            s[11] += fabsf(r2);
         }
-        const float d = fabsf(rho2[i] - rho[i]);
+        const float d = fabsf(r2 - r1);
         if (!(d <= bv)) {  // also takes a non-finite change
             bv = isfinite(d) ? d : INFINITY;
             bi = l;
@@ -1464,9 +1470,9 @@ __global__ void k_tube_checks(const float *rho, const float *u, const float *T, 
     }
     if (threadIdx.x == 0) {
         if (residual) {
-            const double m = fabs(tot[3] - tot[0]) / tot[0];
-            const double j = fabs(tot[4] - tot[1]) / tot[0];
-            const double e = fabs(tot[5] - tot[2]) / tot[2];
+            const double m = fabs(tot[3]) / tot[0];
+            const double j = fabs(tot[4]) / tot[0];
+            const double e = fabs(tot[5]) / tot[2];
             residual[b] = (float)fmax(m, fmax(j, e));
         }
         if (l1) {
