@@ -247,8 +247,10 @@ int lbm_batch_bind(lbm_batch b, void *buf_a, void *buf_b, size_t state_bytes, vo
  * the status words.  Asynchronous. */
 int lbm_batch_set_macro(lbm_batch b, const float *rho, const float *u, const float *T);
 
-/* Advance every problem by k >= 0 steps in one persistent launch.
- * Asynchronous. */
+/* Advance every problem by k >= 0 steps in one persistent launch.  When
+ * the longest problem has at most 864 nodes each block holds its problem's
+ * two state buffers in shared memory for the whole run (same results, bit
+ * for bit).  Asynchronous. */
 int lbm_batch_run(lbm_batch b, int64_t k);
 
 /* rho, u, T of every problem (layout above).  Asynchronous. */

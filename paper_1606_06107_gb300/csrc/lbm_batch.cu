@@ -84,20 +84,20 @@ __device__ __forceinline__ Params<7> tube_params(const BatchParams &bp, const Tu
 }
 
 // One node of one problem: the body of k_step<D1Q7, rot, MODE> with
-// L2-coherent loads.
-template <int MODE>
+// L2-coherent loads (CG = 1) or plain loads from shared memory (CG = 2).
+template <int MODE, int CG = 1>
 __device__ __forceinline__ void batch_node(const Params<7> &p, int x)
 {
     const Offsets o = node_offsets<1>(p, x, 0, 0);
     float g[7], h[7];
-    load_node<kD1, true, MODE, true>(p, o, g, h);
+    load_node<kD1, true, MODE, CG>(p, o, g, h);
     const Moments m = node_moments<kD1, true>(p, g, h);
     if (!(m.rho > 0.f) || !(m.T > 0.f) || !(fabsf(m.T) < 3.0e38f)) atomicOr(p.status, 1);
     collide_store<kD1>(p, o.self(), g, m, [&](auto ic, float gi) {
-        return transport<kD1, MODE, decltype(ic)::value, true>(p, o, gi);
+        return transport<kD1, MODE, decltype(ic)::value, CG>(p, o, gi);
     });
     float adv[7];
-    rot_advect<1, true>(p, o, h, m, adv);
+    rot_advect<1, CG>(p, o, h, m, adv);
     rot_store(p, o.self(), h, m, adv);
 }
 
@@ -121,6 +121,47 @@ __global__ void __launch_bounds__(1024) k_batch_run(const BatchParams bp)
             cur ^= 1;
             __syncthreads();  // step s+1 reads neighbours written in step s
         }
+    }
+}
+
+// The same schedule for problems whose two state buffers fit in shared
+// memory (14 x pitch floats each): the block copies its problem in, steps
+// it between two shared-memory buffers (a step is then bound by shared-
+// memory latency instead of the L2 round trip of each neighbour load), and
+// copies the result to the global buffer the other form would end in.  The
+// node update is the same code, so the results are the same bits.
+template <int MODE>
+__global__ void __launch_bounds__(1024) k_batch_run_sm(const BatchParams bp)
+{
+    extern __shared__ float sm[];
+    __shared__ int claim;
+    for (;;) {
+        if (threadIdx.x == 0) claim = atomicAdd(bp.counter, 1);
+        __syncthreads();
+        const int slot = claim;
+        __syncthreads();  // every thread has read `claim` before it is reused
+        if (slot >= bp.count) return;
+        const int k = bp.order[slot];
+        const TubeDesc d = bp.tubes[k];
+        const int n = 14 * d.pitch;
+        float *a = sm, *c = sm + n;  // a holds the current state
+        const float *in = bp.buf[bp.cur] + d.base;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) a[e] = __ldcg(in + e);
+        __syncthreads();
+        for (long long s = 0; s < bp.steps; ++s) {
+            Params<7> p = tube_params(bp, d, nullptr, nullptr);
+            p.src = a;
+            p.dst = c;
+            p.status = bp.status + k;
+            for (int x = threadIdx.x; x < d.len; x += blockDim.x) batch_node<MODE, 2>(p, x);
+            float *t = a;
+            a = c;
+            c = t;
+            __syncthreads();  // step s+1 reads neighbours written in step s
+        }
+        float *out = bp.buf[bp.cur ^ (int)(bp.steps & 1)] + d.base;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) out[e] = a[e];
+        // the claim's barriers order these reads before the next copy-in
     }
 }
 
@@ -161,6 +202,13 @@ void d1q7(double *r, double w[7])
 
 size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
+// Largest shared-memory state (two buffers of the longest problem) for
+// which a run takes the shared-memory form: 96 KB keeps at least two blocks
+// per SM (problems of up to 864 nodes).
+#ifndef LBM_BATCH_SMEM_MAX
+#define LBM_BATCH_SMEM_MAX (96 * 1024)
+#endif
+
 }  // namespace
 }  // namespace lbm
 
@@ -173,6 +221,7 @@ struct lbm_batch_ctx {
     std::vector<TubeDesc> tubes;
     std::vector<int> order;
     int max_len = 0;
+    int sm_bytes = 0;  // > 0: runs take the shared-memory form with this much per block
     int64_t total_nodes = 0;
     size_t state_floats = 0;
     size_t off_tubes = 0, off_order = 0, off_status = 0, off_counter = 0, work_bytes = 0;
@@ -233,16 +282,29 @@ BatchParams batch_params(const lbm_batch_ctx *b, long long steps)
 
 bool aligned(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
 
+// The persistent kernel of a run: the shared-memory form when the longest
+// problem fits (sm_bytes > 0), else the global-memory form.
+const void *run_kernel(const lbm_batch_ctx *b)
+{
+    if (b->sm_bytes > 0)
+        return (b->mode == LBM_MODE_FD) ? (const void *)lbm::k_batch_run_sm<1>
+                                        : (const void *)lbm::k_batch_run_sm<0>;
+    return (b->mode == LBM_MODE_FD) ? (const void *)lbm::k_batch_run<1>
+                                    : (const void *)lbm::k_batch_run<0>;
+}
+
 // Resident-block grid of the persistent kernel for `threads` per block.
-cudaError_t persistent_grid(int mode, int threads, int bps, int *grid)
+cudaError_t persistent_grid(const lbm_batch_ctx *b, int threads, int bps, int *grid)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = (mode == LBM_MODE_FD)
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::k_batch_run<1>, threads, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::k_batch_run<0>, threads, 0);
+    const void *fn = run_kernel(b);
+    if (b->sm_bytes > 0)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b->sm_bytes);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, b->sm_bytes);
     if (e != cudaSuccess) return e;
     per_sm = std::max(1, per_sm);
     if (bps > 0) per_sm = std::min(per_sm, bps);
@@ -254,7 +316,7 @@ cudaError_t persistent_grid(int mode, int threads, int bps, int *grid)
 int build_graph(lbm_batch b, long long steps, cudaGraphExec_t *exec)
 {
     int grid = 0;
-    cudaError_t e = persistent_grid(b->mode, b->threads, b->blocks_per_sm, &grid);
+    cudaError_t e = persistent_grid(b, b->threads, b->blocks_per_sm, &grid);
     if (e != cudaSuccess) return bcuda(b, e, "occupancy query");
     cudaGraph_t g = nullptr;
     e = cudaGraphCreate(&g, 0);
@@ -271,10 +333,10 @@ int build_graph(lbm_batch b, long long steps, cudaGraphExec_t *exec)
     BatchParams bp = batch_params(b, steps);
     void *args[] = {&bp};
     cudaKernelNodeParams kp{};
-    kp.func = (b->mode == LBM_MODE_FD) ? (void *)lbm::k_batch_run<1> : (void *)lbm::k_batch_run<0>;
+    kp.func = const_cast<void *>(run_kernel(b));
     kp.gridDim = dim3(grid);
     kp.blockDim = dim3(b->threads);
-    kp.sharedMemBytes = 0;
+    kp.sharedMemBytes = (unsigned)b->sm_bytes;
     kp.kernelParams = args;
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_run, g, &n_reset, 1, &kp);
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
@@ -332,6 +394,8 @@ int lbm_batch_create(int count, const int64_t *lengths, const int *n, const doub
     }
     b->state_floats = base;
     b->total_nodes = node;
+    const size_t sm = (size_t)2 * 14 * ((b->max_len + 31) / 32 * 32) * sizeof(float);
+    b->sm_bytes = (sm <= (size_t)LBM_BATCH_SMEM_MAX) ? (int)sm : 0;
     b->order.resize(count);
     std::iota(b->order.begin(), b->order.end(), 0);
     std::stable_sort(b->order.begin(), b->order.end(),

@@ -232,17 +232,19 @@ __device__ __forceinline__ Offsets node_offsets(const Params<Q, ST> &p, int x, i
     return o;
 }
 
-// CG = false: read-only path (the source buffer is never written during the
-// launch).  CG = true: L2-coherent loads, for kernels that read back what
-// the same launch wrote (the persistent ensemble kernel).
-template <bool CG = false, int Q, typename ST>
+// CG = 0: read-only path (the source buffer is never written during the
+// launch).  CG = 1: L2-coherent loads, for kernels that read back what the
+// same launch wrote (the persistent ensemble kernel).  CG = 2: plain
+// generic loads (a state held in shared memory).
+template <int CG = 0, int Q, typename ST>
 __device__ __forceinline__ float ld(const Params<Q, ST> &p, int pop, int off)
 {
     // 32-bit element index up to 49 populations; D3Q343 states exceed 2^32
     using Idx = typename std::conditional<(Q > 49), uint64_t, uint32_t>::type;
     const ST *a = p.src + ((Idx)pop * (Idx)p.S + (Idx)(uint32_t)off);
     ST v;
-    if constexpr (CG) v = __ldcg(a);
+    if constexpr (CG == 2) v = *a;
+    else if constexpr (CG == 1) v = __ldcg(a);
     else v = __ldg(a);
     if constexpr (std::is_same<ST, float>::value) return v;
     else return Storage<ST>::decode(v, pop < Q ? p.w[pop] : p.wr[pop - Q]);
@@ -445,7 +447,7 @@ __device__ __forceinline__ void heq_node(const Params<Q, ST> &p, float T, float 
 // convection by u at Courant number u * nu_scale, BGK toward h^eq(T).
 // (Issuing these neighbour loads right after the moments, before the
 // translational work, measured 9 % slower on the 2048^2 workload.)
-template <int D, bool CG = false, int Q, typename ST>
+template <int D, int CG = 0, int Q, typename ST>
 __device__ __forceinline__ void rot_advect(const Params<Q, ST> &p, const Offsets &o,
                                            const float *h, const Moments &m, float *adv)
 {
@@ -483,7 +485,7 @@ __device__ __forceinline__ void rot_store(const Params<Q, ST> &p, int self, cons
 // Load the time-t populations of one node.  STREAM: pull g_i(x) = ft_i(x - e_i).
 // FD: g_i(x) = ft_i(x).
 
-template <int LAT, bool ROT, int MODE, bool CG = false, int Q, typename ST>
+template <int LAT, bool ROT, int MODE, int CG = 0, int Q, typename ST>
 __device__ __forceinline__ void load_node(const Params<Q, ST> &p, const Offsets &o, float *g,
                                           float *h)
 {
@@ -504,7 +506,7 @@ __device__ __forceinline__ void load_node(const Params<Q, ST> &p, const Offsets 
 // FD transport of one translational population (Eq. DisEvolSpaTiI): the
 // upwind side of each axis is fixed by the sign of e_ia, the Courant number
 // is |e_ia| / m.
-template <int LAT, int I, bool CG = false, int Q, typename ST>
+template <int LAT, int I, int CG = 0, int Q, typename ST>
 __device__ __forceinline__ float fd_convect(const Params<Q, ST> &p, const Offsets &o, float g0)
 {
     using L = Lattice<LAT>;
@@ -524,7 +526,7 @@ __device__ __forceinline__ float fd_convect(const Params<Q, ST> &p, const Offset
     return adv;
 }
 
-template <int LAT, int MODE, int I, bool CG = false, int Q, typename ST>
+template <int LAT, int MODE, int I, int CG = 0, int Q, typename ST>
 __device__ __forceinline__ float transport(const Params<Q, ST> &p, const Offsets &o, float g0)
 {
     if constexpr (MODE == 1) return fd_convect<LAT, I, CG>(p, o, g0);
@@ -699,7 +701,7 @@ __global__ void __launch_bounds__(kBlockX) k_init(const Params<Lattice<LAT>::Q, 
 // ---------------------------------------------------------------------------
 // rho, u, T of the current state into unpadded caller arrays.
 
-template <int LAT, bool ROT, int MODE, bool CG = false, typename ST>
+template <int LAT, bool ROT, int MODE, int CG = 0, typename ST>
 __device__ __forceinline__ void moments_node(const Params<Lattice<LAT>::Q, ST> &p, int x, int y, int z)
 {
     using L = Lattice<LAT>;

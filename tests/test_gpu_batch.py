@@ -37,11 +37,18 @@ def plain_run(spec, rho, u, T, mode, m_fd, steps):
     return [x.cpu().numpy().reshape(-1) for x in s.moments()]
 
 
+# Ensembles whose longest problem has at most 864 nodes run with the state in
+# shared memory (k_batch_run_sm); SPECS (up to 1000 nodes) takes the global
+# form, SHORT the shared-memory one.
+SHORT = [s for s in SPECS if s[0] <= 864]
+
+
+@pytest.mark.parametrize("specs", [SPECS, SHORT], ids=["global", "shared"])
 @pytest.mark.parametrize("mode,m_fd", [("fd", 10), ("stream", 1)])
-def test_batch_bitwise_equals_single_runs(mode, m_fd):
+def test_batch_bitwise_equals_single_runs(mode, m_fd, specs):
     from paper_1606_06107_gb300 import LbmBatch
-    rho, u, T = tubes(SPECS)
-    b = LbmBatch([s[0] for s in SPECS], [s[1] for s in SPECS], [s[2] for s in SPECS],
+    rho, u, T = tubes(specs)
+    b = LbmBatch([s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs],
                  mode=mode, m_fd=m_fd)
     b.set_macro(rho, u, T)
     b.run(20)
@@ -49,7 +56,7 @@ def test_batch_bitwise_equals_single_runs(mode, m_fd):
     got = [x.cpu().numpy() for x in b.moments()]
     st, bad = b.status()
     assert bad == 0
-    for k, spec in enumerate(SPECS):
+    for k, spec in enumerate(specs):
         sl = slice(b.offsets[k], b.offsets[k] + spec[0])
         ref = plain_run(spec, rho[sl], u[sl], T[sl], mode, m_fd, 51)
         for a, r in zip(got, ref):
@@ -76,13 +83,14 @@ def test_batch_matches_oracle(orc):
             assert np.abs(a[sl] - r).sum() / np.abs(r).sum() <= 1e-5
 
 
-def test_batch_status_flags_only_the_bad_problem():
+@pytest.mark.parametrize("specs", [SPECS, SHORT], ids=["global", "shared"])
+def test_batch_status_flags_only_the_bad_problem(specs):
     from paper_1606_06107_gb300 import LbmBatch
-    rho, u, T = tubes(SPECS)
+    rho, u, T = tubes(specs)
     T = T.copy()
     k = 3
-    T[int(np.sum([s[0] for s in SPECS[:k]])) + 5] = -1.0
-    b = LbmBatch([s[0] for s in SPECS], [s[1] for s in SPECS], [s[2] for s in SPECS])
+    T[int(np.sum([s[0] for s in specs[:k]])) + 5] = -1.0
+    b = LbmBatch([s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs])
     b.set_macro(rho, u, T)
     b.run(3)
     st, bad = b.status()
