@@ -238,6 +238,14 @@ int lbm_batch_set_problems(lbm_batch b, const int *n, const double *tau);
 /* Bytes for each state buffer and for the work buffer; total node count. */
 int lbm_batch_sizes(lbm_batch b, size_t *state_bytes, size_t *work_bytes, int64_t *total_nodes);
 
+/* Restrict, per problem, the nodes whose failure (non-finite or
+ * non-positive rho or T) sets the status word to [lo[k], hi[k]) (host
+ * arrays, 0 <= lo <= hi <= length); lo = hi = NULL restores whole
+ * problems.  A window of a longer problem run with margins reports only
+ * failures of its exact interior.  Keeps the state and the cached graphs;
+ * no counterpart in the paper. */
+int lbm_batch_set_watch(lbm_batch b, const int *lo, const int *hi);
+
 /* Bind caller memory and the stream; uploads the per-problem table
  * (asynchronously, from host memory owned by the handle). */
 int lbm_batch_bind(lbm_batch b, void *buf_a, void *buf_b, size_t state_bytes, void *work,

@@ -33,6 +33,8 @@ struct TubeDesc {    // one problem, indexed by its original position
     float cT;        // (D + n)/2
     float half_n;    // n/2
     float half_n_r2; // n r^2 / 2
+    int watch_lo;    // nodes [watch_lo, watch_hi) set the status word
+    int watch_hi;
 };
 
 struct BatchParams {
@@ -86,13 +88,15 @@ __device__ __forceinline__ Params<7> tube_params(const BatchParams &bp, const Tu
 // One node of one problem: the body of k_step<D1Q7, rot, MODE> with
 // L2-coherent loads (CG = 1) or plain loads from shared memory (CG = 2).
 template <int MODE, int CG = 1>
-__device__ __forceinline__ void batch_node(const Params<7> &p, int x)
+__device__ __forceinline__ void batch_node(const Params<7> &p, const TubeDesc &d, int x)
 {
     const Offsets o = node_offsets<1>(p, x, 0, 0);
     float g[7], h[7];
     load_node<kD1, true, MODE, CG>(p, o, g, h);
     const Moments m = node_moments<kD1, true>(p, g, h);
-    if (!(m.rho > 0.f) || !(m.T > 0.f) || !(fabsf(m.T) < 3.0e38f)) atomicOr(p.status, 1);
+    if ((!(m.rho > 0.f) || !(m.T > 0.f) || !(fabsf(m.T) < 3.0e38f)) && x >= d.watch_lo &&
+        x < d.watch_hi)
+        atomicOr(p.status, 1);
     collide_store<kD1>(p, o.self(), g, m, [&](auto ic, float gi) {
         return transport<kD1, MODE, decltype(ic)::value, CG>(p, o, gi);
     });
@@ -117,7 +121,7 @@ __global__ void __launch_bounds__(1024) k_batch_run(const BatchParams bp)
         for (long long s = 0; s < bp.steps; ++s) {
             Params<7> p = tube_params(bp, d, bp.buf[cur], bp.buf[cur ^ 1]);
             p.status = bp.status + k;
-            for (int x = threadIdx.x; x < d.len; x += blockDim.x) batch_node<MODE>(p, x);
+            for (int x = threadIdx.x; x < d.len; x += blockDim.x) batch_node<MODE>(p, d, x);
             cur ^= 1;
             __syncthreads();  // step s+1 reads neighbours written in step s
         }
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(1024) k_batch_run_sm(const BatchParams bp)
             p.src = a;
             p.dst = c;
             p.status = bp.status + k;
-            for (int x = threadIdx.x; x < d.len; x += blockDim.x) batch_node<MODE, 2>(p, x);
+            for (int x = threadIdx.x; x < d.len; x += blockDim.x) batch_node<MODE, 2>(p, d, x);
             float *t = a;
             a = c;
             c = t;
@@ -384,6 +388,8 @@ int lbm_batch_create(int count, const int64_t *lengths, const int *n, const doub
         d.cT = (float)(0.5 * (1 + n[k]));
         d.half_n = (float)(0.5 * n[k]);
         d.half_n_r2 = (float)(0.5 * n[k] * b->r * b->r);
+        d.watch_lo = 0;
+        d.watch_hi = d.len;
         base += (size_t)14 * d.pitch;
         node += d.len;
         b->max_len = std::max(b->max_len, d.len);
@@ -432,6 +438,26 @@ int lbm_batch_set_problems(lbm_batch b, const int *n, const double *tau)
                                         b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "table upload");
         b->has_state = false;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_set_watch(lbm_batch b, const int *lo, const int *hi)
+{
+    if (!b) return LBM_EINVAL;
+    if ((lo == nullptr) != (hi == nullptr)) return bfail(b, LBM_EINVAL, "lo and hi go together");
+    for (int k = 0; lo && k < b->count; ++k)
+        if (lo[k] < 0 || lo[k] > hi[k] || hi[k] > b->tubes[k].len)
+            return bfail(b, LBM_EINVAL, "watch range outside the problem");
+    for (int k = 0; k < b->count; ++k) {
+        b->tubes[k].watch_lo = lo ? lo[k] : 0;
+        b->tubes[k].watch_hi = lo ? hi[k] : b->tubes[k].len;
+    }
+    if (b->bound) {
+        cudaError_t e = cudaMemcpyAsync(b->work + b->off_tubes, b->tubes.data(),
+                                        sizeof(TubeDesc) * b->count, cudaMemcpyHostToDevice,
+                                        b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "table upload");
     }
     return LBM_OK;
 }

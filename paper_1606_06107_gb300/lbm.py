@@ -59,6 +59,8 @@ SIGNATURES = {
                                         ctypes.c_int, ctypes.POINTER(_vp)]),
     "lbm_batch_set_problems": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_double)]),
+    "lbm_batch_set_watch": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t),
                                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i64)]),
     "lbm_batch_bind": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t,
@@ -402,6 +404,19 @@ class LbmBatch:
             self._check(self.lib.lbm_batch_set_problems(
                 self.h, nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                 tt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def set_watch(self, lo=None, hi=None):
+        """Only nodes [lo[k], hi[k]) of problem k set its status word
+        (lbm_batch_set_watch); no arguments: whole problems."""
+        if lo is None:
+            self._check(self.lib.lbm_batch_set_watch(self.h, None, None))
+            return
+        ll = np.ascontiguousarray(np.broadcast_to(lo, (self.count,)), dtype=np.int32)
+        hh = np.ascontiguousarray(np.broadcast_to(hi, (self.count,)), dtype=np.int32)
+        with self.torch.cuda.device(self.device):
+            self._check(self.lib.lbm_batch_set_watch(
+                self.h, ll.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                hh.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
 
     def set_block(self, threads: int, blocks_per_sm: int = 0):
         self._check(self.lib.lbm_batch_set_block(self.h, int(threads), int(blocks_per_sm)))

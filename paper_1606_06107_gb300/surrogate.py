@@ -531,11 +531,14 @@ class SurrogateRunner:
     """
 
     def __init__(self, net: ConvOperator, n, tau, L, K, tol=1e-2, window=256, m_fd=10,
-                 timing=False):
+                 timing=False, fallback_window=512):
         import torch
         self.net, self.torch = net, torch
         self.n = np.asarray(n)
         self.B, self.L, self.K, self.tau, self.tol, self.m_fd = len(n), L, K, tau, tol, m_fd
+        # fallback tubes are recomputed as windows of fallback_window nodes
+        # (plus the 2K-node margins), each an exact piece of the full run
+        self.fb_window = max(1, min(int(fallback_window), L))
         self.gamma_np = np.array([GAMMA_OF_N[int(v)] for v in self.n])
         dev = net.device
         self.gamma = torch.as_tensor(self.gamma_np.astype(np.float32), device=dev)
@@ -621,38 +624,69 @@ class SurrogateRunner:
         return (r2, u2, T2), fallback
 
     def _fallback(self, rho, u, T, out, tubes):
+        """Recompute `tubes` with the method.  Each tube is cut into windows
+        whose interiors (fb_window nodes) tile it, each window carrying the
+        2K-node margins on its inner sides: the method on a window gives its
+        interior bit for bit as the full-tube run does (the spot check's
+        property), and short windows run many to a launch with their state
+        in shared memory.  Only a window's interior may set its status word
+        (lbm_batch_set_watch), so a window fails exactly where the full-tube
+        run fails; a tube on which any window fails keeps its prediction and
+        is quarantined."""
         t, net, lib = self.torch, self.net, self.net.lib
+        L, M = self.L, self.margin
+        Wi = self.fb_window
+        S = min(L, Wi + 2 * M)
+        if S == L:  # one window: the whole tube
+            Wi, istart, wstart = L, np.zeros(1, np.int64), np.zeros(1, np.int64)
+        else:
+            nw = -(-L // Wi)
+            istart = np.minimum(np.arange(nw) * Wi, L - Wi)     # the last one may overlap
+            wstart = np.clip(istart - M, 0, L - S)
+        nw = istart.size
         f = len(tubes)
-        # a pool of solvers with room for 1, 2, 4, ... tubes of length L,
-        # retargeted to the tubes of this call (lbm_batch_set_problems); the
-        # free slots repeat the last tube and their results are dropped
-        cap = 1 << (f - 1).bit_length()
+        count = f * nw
+        # a pool of solvers with room for 1, 2, 4, ... windows of S nodes,
+        # retargeted to this call's windows (lbm_batch_set_problems); the
+        # free slots repeat the last window and their results are dropped
+        cap = 1 << (count - 1).bit_length()
         lb = self._solvers.get(cap)
         if lb is None:
-            lb = LbmBatch([self.L] * cap, [0] * cap, [self.tau] * cap, mode="fd", m_fd=self.m_fd,
+            lb = LbmBatch([S] * cap, [0] * cap, [self.tau] * cap, mode="fd", m_fd=self.m_fd,
                           device=net.device)
-            lb.set_block(_latency_block(self.L))
+            lb.set_block(_latency_block(S))
             self._solvers[cap] = lb
-        padded = np.concatenate([tubes, np.full(cap - f, tubes[-1])]).astype(np.int64)
-        lb.set_problems(self.n[padded], self.tau)
-        rows = t.as_tensor(padded, device=net.device)
-        packed = _rows(lib, t, net.device, (rho, u, T), rows, None, self.L, self.L)
+        win_tube = np.repeat(np.asarray(tubes, np.int64), nw)
+        win_start = np.tile(wstart, f)
+        pad = cap - count
+        rows_np = np.concatenate([win_tube, np.full(pad, win_tube[-1])])
+        offs_np = np.concatenate([win_start, np.full(pad, win_start[-1])])
+        lb.set_problems(self.n[rows_np], self.tau)
+        # only the exact interiors report failures (the margins carry the
+        # windows' artificial ends)
+        inner_np = np.tile(istart - wstart, f)
+        lo = np.concatenate([inner_np, np.full(pad, inner_np[-1])])
+        lb.set_watch(lo, lo + Wi)
+        rows = t.as_tensor(rows_np, device=net.device)
+        offs = t.as_tensor(offs_np.astype(np.int32), device=net.device)
+        packed = _rows(lib, t, net.device, (rho, u, T), rows, offs, S, L)
         lb.set_macro(*packed)
         lb.run(self.K)
-        res = [x[:f * self.L] for x in lb.moments()]
-        rows = rows[:f]
+        res = lb.moments()
         # where the method itself fails (non-finite or non-positive rho, T from
         # a state at the edge of its stability), the prediction is kept and the
         # tube is counted; everywhere else the method's result replaces it
         st, _ = lb.status()
-        failed = np.flatnonzero(st[:f] != 0)
-        if failed.size:
-            self.stats["method_failed"] += int(failed.size)
-            self.quarantined[tubes[failed]] = True
-            good = np.flatnonzero(st[:f] == 0)
-            if good.size == 0:
-                return
-            keep = t.as_tensor(good.astype(np.int64), device=net.device)
-            res = _rows(lib, t, net.device, res, keep, None, self.L, self.L)
-            rows = t.as_tensor(tubes[good].astype(np.int64), device=net.device)
-        _scatter(lib, t, net.device, res, rows, None, self.L, self.L, out)
+        failed = (st[:count] != 0).reshape(f, nw).any(1)
+        if failed.any():
+            self.stats["method_failed"] += int(failed.sum())
+            self.quarantined[np.asarray(tubes)[failed]] = True
+        keep = np.flatnonzero(np.repeat(~failed, nw))
+        if keep.size == 0:
+            return
+        inner = (np.tile(istart - wstart, f)[keep]).astype(np.int32)
+        interiors = _rows(lib, t, net.device, res, t.as_tensor(keep, device=net.device),
+                          t.as_tensor(inner, device=net.device), Wi, S)
+        _scatter(lib, t, net.device, interiors, t.as_tensor(win_tube[keep], device=net.device),
+                 t.as_tensor(np.tile(istart, f)[keep].astype(np.int32), device=net.device), Wi,
+                 L, out)

@@ -146,3 +146,29 @@ def test_set_problems_retargets_the_ensemble():
     got = [x.cpu().numpy() for x in b.moments()]
     for a, r in zip(got, want):
         assert np.array_equal(a, r)
+
+
+@pytest.mark.parametrize("specs", [SPECS, SHORT], ids=["global", "shared"])
+def test_watch_range_limits_the_status_word(specs):
+    """A failure planted outside a problem's watch range leaves its status
+    word clear; inside it, the word is set (lbm_batch_set_watch)."""
+    from paper_1606_06107_gb300 import LbmBatch
+    k = 3                                 # 257 nodes
+    node = 200
+    rho, u, T = tubes(specs)
+    T = T.copy()
+    T[int(np.sum([s[0] for s in specs[:k]])) + node] = -1.0
+    lengths = [s[0] for s in specs]
+    b = LbmBatch(lengths, [s[1] for s in specs], [s[2] for s in specs])
+    lo, hi = np.zeros(len(specs), int), np.array(lengths)
+    hi[k] = node - 10                     # watch [0, 190): the bad node is outside
+    b.set_watch(lo, hi)
+    b.set_macro(rho, u, T)
+    b.run(1)
+    st, bad = b.status()
+    assert bad == 0
+    b.set_watch()                         # whole problems again
+    b.set_macro(rho, u, T)
+    b.run(1)
+    st, bad = b.status()
+    assert bad == 1 and st[k] != 0

@@ -300,9 +300,12 @@ def test_spot_window_equals_full_tube_method(lbmlib):
         np.testing.assert_array_equal(a, r[:, off:off + W])
 
 
-def test_runner_falls_back_to_the_method(lbmlib):
+@pytest.mark.parametrize("fb_window", [512, 100])
+def test_runner_falls_back_to_the_method(lbmlib, fb_window):
     """An untrained network fails its checks everywhere; every tube is then
-    recomputed by the method and the call returns exactly L_K(state)."""
+    recomputed by the method and the call returns exactly L_K(state): as
+    whole tubes (window 512 = L) or as 6 windows of 100 interior nodes with
+    64-node margins (the last one overlapping its neighbour)."""
     torch = _t()
     from paper_1606_06107_gb300 import LbmBatch
     from paper_1606_06107_gb300.surrogate import ConvOperator, SurrogateRunner
@@ -314,7 +317,7 @@ def test_runner_falls_back_to_the_method(lbmlib):
     arrays[-2] = np.zeros_like(arrays[-2])
     arrays[-1] = np.array([0.3, 0.3, 0.3])
     net.set_params(arrays)
-    run = SurrogateRunner(net, n, tau, L, K)
+    run = SurrogateRunner(net, n, tau, L, K, fallback_window=fb_window)
     g = [f32(v) for v in (rho, u, T)]
     (r2, u2, T2), fb = run.advance(*g)
     assert sorted(fb.tolist()) == list(range(B))
