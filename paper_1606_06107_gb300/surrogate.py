@@ -556,6 +556,7 @@ class SurrogateRunner:
         self.inner = torch.full((B,), self.margin, dtype=torch.int32, device=dev)
         self.residual = torch.empty(B, dtype=torch.float32, device=dev)
         self.l1 = torch.empty(B, dtype=torch.float32, device=dev)
+        self._checks_h = torch.empty((2, B), dtype=torch.float32).pin_memory()
         self.stats = {"calls": 0, "fallback_tubes": 0, "max_residual": 0.0, "max_l1": 0.0,
                       "method_failed": 0}
         self.quarantined = np.zeros(self.B, dtype=bool)
@@ -604,8 +605,11 @@ class SurrogateRunner:
         if rc != 0:
             raise LbmError(rc, "lbm_nn_tube_checks")
         ev = self._mark("decide", ev)
-        res = self.residual.cpu().numpy()
-        l1 = self.l1.cpu().numpy()
+        self._checks_h[0].copy_(self.residual, non_blocking=True)
+        self._checks_h[1].copy_(self.l1, non_blocking=True)
+        t.cuda.current_stream(net.device).synchronize()
+        res = self._checks_h[0].numpy().copy()
+        l1 = self._checks_h[1].numpy().copy()
         bad = ~np.isfinite(res) | (res > self.tol) | ~np.isfinite(l1) | (l1 > self.tol)
         # a tube on which the method itself has failed is not sent back to it
         fallback = np.flatnonzero(bad & ~self.quarantined)
@@ -647,46 +651,60 @@ class SurrogateRunner:
         f = len(tubes)
         count = f * nw
         # a pool of solvers with room for 1, 2, 4, ... windows of S nodes,
-        # retargeted to this call's windows (lbm_batch_set_problems); the
-        # free slots repeat the last window and their results are dropped
+        # retargeted to this call's windows (lbm_batch_set_problems); slot i
+        # is always window i % nw, so the window geometry (offsets, watch
+        # ranges) is fixed per pool entry; the free slots repeat the last
+        # tube and their results are dropped
         cap = 1 << (count - 1).bit_length()
-        lb = self._solvers.get(cap)
-        if lb is None:
+        ent = self._solvers.get(cap)
+        if ent is None:
             lb = LbmBatch([S] * cap, [0] * cap, [self.tau] * cap, mode="fd", m_fd=self.m_fd,
                           device=net.device)
             lb.set_block(_latency_block(S))
-            self._solvers[cap] = lb
+            slot = np.arange(cap) % nw
+            inner = (istart - wstart)[slot]
+            # only the exact interiors report failures (the margins carry the
+            # windows' artificial ends)
+            lb.set_watch(inner, inner + Wi)
+            dev = net.device
+            ent = {"lb": lb,
+                   "woff": t.as_tensor(wstart[slot].astype(np.int32), device=dev),
+                   "inner": t.as_tensor(inner.astype(np.int32), device=dev),
+                   "ioff": t.as_tensor(istart[slot].astype(np.int32), device=dev),
+                   "all": t.arange(cap, dtype=t.int64, device=dev),
+                   "rows_h": t.empty(cap, dtype=t.int64).pin_memory(),
+                   "rows": t.empty(cap, dtype=t.int64, device=dev)}
+            self._solvers[cap] = ent
+        lb = ent["lb"]
         win_tube = np.repeat(np.asarray(tubes, np.int64), nw)
-        win_start = np.tile(wstart, f)
-        pad = cap - count
-        rows_np = np.concatenate([win_tube, np.full(pad, win_tube[-1])])
-        offs_np = np.concatenate([win_start, np.full(pad, win_start[-1])])
+        rows_np = np.concatenate([win_tube, np.full(cap - count, win_tube[-1])])
         lb.set_problems(self.n[rows_np], self.tau)
-        # only the exact interiors report failures (the margins carry the
-        # windows' artificial ends)
-        inner_np = np.tile(istart - wstart, f)
-        lo = np.concatenate([inner_np, np.full(pad, inner_np[-1])])
-        lb.set_watch(lo, lo + Wi)
-        rows = t.as_tensor(rows_np, device=net.device)
-        offs = t.as_tensor(offs_np.astype(np.int32), device=net.device)
-        packed = _rows(lib, t, net.device, (rho, u, T), rows, offs, S, L)
+        ent["rows_h"].numpy()[:] = rows_np
+        rows = ent["rows"]
+        rows.copy_(ent["rows_h"], non_blocking=True)
+        packed = _rows(lib, t, net.device, (rho, u, T), rows, ent["woff"], S, L)
         lb.set_macro(*packed)
         lb.run(self.K)
         res = lb.moments()
         # where the method itself fails (non-finite or non-positive rho, T from
         # a state at the edge of its stability), the prediction is kept and the
         # tube is counted; everywhere else the method's result replaces it
-        st, _ = lb.status()
+        st, _ = lb.status()      # (synchronises: rows_h may be rewritten after it)
         failed = (st[:count] != 0).reshape(f, nw).any(1)
-        if failed.any():
+        if not failed.any():
+            sel, dst_rows, dst_off, inner = (ent["all"][:count], rows[:count],
+                                             ent["ioff"][:count], ent["inner"][:count])
+        else:
             self.stats["method_failed"] += int(failed.sum())
             self.quarantined[np.asarray(tubes)[failed]] = True
-        keep = np.flatnonzero(np.repeat(~failed, nw))
-        if keep.size == 0:
-            return
-        inner = (np.tile(istart - wstart, f)[keep]).astype(np.int32)
-        interiors = _rows(lib, t, net.device, res, t.as_tensor(keep, device=net.device),
-                          t.as_tensor(inner, device=net.device), Wi, S)
-        _scatter(lib, t, net.device, interiors, t.as_tensor(win_tube[keep], device=net.device),
-                 t.as_tensor(np.tile(istart, f)[keep].astype(np.int32), device=net.device), Wi,
-                 L, out)
+            keep = np.flatnonzero(np.repeat(~failed, nw))
+            if keep.size == 0:
+                return
+            dev = net.device
+            slot = keep % nw
+            sel = t.as_tensor(keep, device=dev)
+            dst_rows = t.as_tensor(win_tube[keep], device=dev)
+            dst_off = t.as_tensor(istart[slot].astype(np.int32), device=dev)
+            inner = t.as_tensor((istart - wstart)[slot].astype(np.int32), device=dev)
+        interiors = _rows(lib, t, net.device, res, sel, inner, Wi, S)
+        _scatter(lib, t, net.device, interiors, dst_rows, dst_off, Wi, L, out)

@@ -326,6 +326,23 @@ def test_runner_falls_back_to_the_method(lbmlib, fb_window):
     lb.run(K)
     for a, r in zip((r2, u2, T2), lb.moments()):
         np.testing.assert_array_equal(host(a), host(r))
+    # a tube on which the method fails (a non-positive T planted at node 300)
+    # keeps the prediction and is quarantined; the others get the method
+    Tb = np.array(T, dtype=np.float64).reshape(B, L)
+    Tb[2, 300] = -1.0
+    gb = [f32(rho), f32(u), f32(Tb.reshape(-1))]
+    run_b = SurrogateRunner(net, n, tau, L, K, fallback_window=fb_window)
+    (r4, _, _), fb = run_b.advance(*gb)
+    assert sorted(fb.tolist()) == list(range(B))
+    assert run_b.quarantined.tolist() == [False, False, True, False]
+    assert run_b.stats["method_failed"] == 1
+    lb.set_macro(rho, u, Tb.reshape(-1))
+    lb.run(K)
+    got, want = host(r4).reshape(B, L), host(lb.moments()[0]).reshape(B, L)
+    for k in (0, 1, 3):
+        np.testing.assert_array_equal(got[k], want[k])
+    np.testing.assert_allclose(got[2], np.float32(rho).reshape(B, L)[2] + np.float32(0.3),
+                               rtol=1e-6)
     # with an infinite tolerance nothing falls back and the prediction stands
     run_inf = SurrogateRunner(net, n, tau, L, K, tol=np.inf)
     (r3, _, _), fb = run_inf.advance(*g)
