@@ -1082,39 +1082,47 @@ int grid_for(int64_t n, int threads = 256)
 
 // x0[p][c] = bf16(sum_j feat[p][j] Wl[c][j] + bl[c]).  A block of C threads
 // takes a range of positions: it first copies their feature rows to shared
-// memory with coalesced 16-byte loads, then thread c (row c of the weights in
-// registers) forms channel c of every position from broadcast reads, so each
-// position's C outputs are one coalesced row.
+// memory with coalesced 16-byte loads, then thread t forms channels 2(t mod
+// C/2) and 2(t mod C/2) + 1 (their weight rows in registers) of every other
+// position from broadcast reads, so a warp stores 64 consecutive channels of
+// a position (128 bytes) per instruction.
 template <int F>
 __global__ void k_lift(const float *feat, const float *Wl, const float *bl, __nv_bfloat16 *x0,
                        int64_t P, int C, int64_t per_block)
 {
     extern __shared__ float4 fsh[];  // [per_block][F / 4]
-    const int c = threadIdx.x;
-    float w[F];
+    const int half = C / 2;
+    const int cp = threadIdx.x % half, par = threadIdx.x / half, c = 2 * cp;
+    float w0[F], w1[F];
 #pragma unroll
     for (int j = 0; j < F / 4; ++j) {
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(Wl + c * F) + j);
-        w[4 * j] = q.x, w[4 * j + 1] = q.y, w[4 * j + 2] = q.z, w[4 * j + 3] = q.w;
+        const float4 q0 = __ldg(reinterpret_cast<const float4 *>(Wl + c * F) + j);
+        const float4 q1 = __ldg(reinterpret_cast<const float4 *>(Wl + (c + 1) * F) + j);
+        w0[4 * j] = q0.x, w0[4 * j + 1] = q0.y, w0[4 * j + 2] = q0.z, w0[4 * j + 3] = q0.w;
+        w1[4 * j] = q1.x, w1[4 * j + 1] = q1.y, w1[4 * j + 2] = q1.z, w1[4 * j + 3] = q1.w;
     }
-    const float bias = bl[c];
+    const float bias0 = bl[c], bias1 = bl[c + 1];
     const int64_t p0 = blockIdx.x * per_block, p1 = std::min(P, p0 + per_block);
     const int n4 = (int)(p1 - p0) * (F / 4);
     const float4 *src = reinterpret_cast<const float4 *>(feat + p0 * F);
-    for (int e = c; e < n4; e += blockDim.x) fsh[e] = __ldg(src + e);
+    for (int e = threadIdx.x; e < n4; e += blockDim.x) fsh[e] = __ldg(src + e);
     __syncthreads();
-    for (int64_t p = p0; p < p1; ++p) {
+    for (int64_t p = p0 + par; p < p1; p += 2) {
         const float4 *f = fsh + (p - p0) * (F / 4);
-        float acc = bias;
+        float acc0 = bias0, acc1 = bias1;
 #pragma unroll
         for (int j = 0; j < F / 4; ++j) {
             const float4 v = f[j];
-            acc = fmaf(v.x, w[4 * j], acc);
-            acc = fmaf(v.y, w[4 * j + 1], acc);
-            acc = fmaf(v.z, w[4 * j + 2], acc);
-            acc = fmaf(v.w, w[4 * j + 3], acc);
+            acc0 = fmaf(v.x, w0[4 * j], acc0);
+            acc0 = fmaf(v.y, w0[4 * j + 1], acc0);
+            acc0 = fmaf(v.z, w0[4 * j + 2], acc0);
+            acc0 = fmaf(v.w, w0[4 * j + 3], acc0);
+            acc1 = fmaf(v.x, w1[4 * j], acc1);
+            acc1 = fmaf(v.y, w1[4 * j + 1], acc1);
+            acc1 = fmaf(v.z, w1[4 * j + 2], acc1);
+            acc1 = fmaf(v.w, w1[4 * j + 3], acc1);
         }
-        x0[p * C + c] = __float2bfloat16_rn(acc);
+        *reinterpret_cast<__nv_bfloat162 *>(x0 + p * C + c) = __floats2bfloat162_rn(acc0, acc1);
     }
 }
 
