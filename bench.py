@@ -588,11 +588,14 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"riemann_2d_mild {side}x{side} sample of the "
-                   f"{X}x{Y} D2Q49+D1Q7 n=3 periodic STREAM problem (FP64 CPU oracle)"},
+        # the workload of the measured arm; each step runs a bounded sample of it
+        "config": {"workload": f"{wl.name} {X}x{Y} {LATTICE}+D1Q7 n={NROT} tau=2/3 periodic "
+                               f"STREAM, seed=rank", "nodes_per_gpu": X * Y,
+                   "bytes_per_node_step": BYTES_PER_NODE, "parallelism": "replicas x1"},
         "cpu_baseline": {"value": value, "unit": "Mnode-updates/s", "cores": threads,
                          "kind": "oracle",
-                         "sample": f"{side}x{side} grid, {args.steps} steps"},
+                         "sample": f"a {side}x{side} grid of the same problem per step "
+                                   f"(FP64 oracle), {args.steps} timed steps"},
         "e2e": {"value": value, "unit": "Mnode-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
