@@ -4,7 +4,8 @@
 // 343 populations do not fit in registers, so the step reads its pulled
 // populations twice: a first pass accumulates rho, j and sum |e|^2 g (row
 // sums by (e_y, e_z), column sums by e_x), a second pass re-reads each value
-// (from L1/L2: a 128-node block touches 343 x 128 x 4 B = 175 KB between the
+// (from a shared-memory stash for the first planes with 16-bit storage, else
+// from L1/L2: a 128-node block touches 343 x 128 x 4 B = 175 KB between the
 // two reads) and writes its post-collision value.  The second pass walks the
 // e_z planes in reverse, so that it starts on the lines the first pass loaded
 // last, which are the ones still in L1 (7 % faster with float storage, 1 %
@@ -26,6 +27,33 @@ constexpr int kQ343 = 343;
 #ifndef LBM_Q343_MIN_BLOCKS
 #define LBM_Q343_MIN_BLOCKS 3
 #endif
+// Shared-memory stash of the first pass's raw values for the e_z planes
+// c < NS, which the second pass (walking the planes in reverse) reaches
+// last, when L1 has long evicted them.  6 planes of 16-bit values take
+// 75.3 KB per 128-thread block (3 blocks per SM still fit) and made the
+// 384^3 f16 blast 9 % (n = 0) and 8 % (n = 4) faster (ms per step, n = 0 /
+// n = 4: none 36.2 / 42.2, 4 planes 35.2 / 41.3, 5 33.3 / 39.4, 6 33.0 /
+// 38.8, all 7 at 2 blocks per SM 43.9 / 46.9); float storage gained nothing
+// from 2 planes.  The second pass decodes the same stored bits, so results
+// are unchanged.
+#ifndef LBM_Q343_STASH_HALF
+#define LBM_Q343_STASH_HALF 6
+#endif
+#ifndef LBM_Q343_STASH_FLOAT
+#define LBM_Q343_STASH_FLOAT 0
+#endif
+template <typename ST> struct StashPlanes {
+    static constexpr int value = std::is_same<ST, float>::value ? LBM_Q343_STASH_FLOAT : LBM_Q343_STASH_HALF;
+};
+template <typename ST> constexpr size_t stash_bytes() { return (size_t)StashPlanes<ST>::value * 49 * kBlockX * sizeof(ST); }
+
+template <int Q, typename ST>
+__device__ __forceinline__ float decode_pop(const Params<Q, ST> &p, int pop, ST v)
+{
+    if constexpr (std::is_same<ST, float>::value) return v;
+    else return Storage<ST>::decode(v, p.w[pop]);
+}
+
 template <bool ROT, typename ST>
 __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(const Params<kQ343, ST> p)
 {
@@ -42,8 +70,12 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
 #pragma unroll
     for (int a = 0; a < 7; ++a) cs[a] = 0.f;
     float rho = 0.f, jy = 0.f, jz = 0.f, e2yz = 0.f;
+    extern __shared__ unsigned char q343_smem[];
+    ST *stash = reinterpret_cast<ST *>(q343_smem);  // [NS planes x 49][kBlockX] raw values
+    constexpr int NS = StashPlanes<ST>::value;
     // e_y is unrolled so that each e_z plane issues its 49 loads at once
-    for (int c = 0; c < 7; ++c) {
+    auto plane1 = [&](auto keep, int c) {
+        constexpr bool KEEP = decltype(keep)::value;
         const int zo = bc_wrap(z - (c - 3), p.Z, p.bc2) * plane;
 #pragma unroll
         for (int b = 0; b < 7; ++b) {
@@ -51,7 +83,10 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
             float rsum = 0.f;
 #pragma unroll
             for (int a = 0; a < 7; ++a) {
-                const float g = ld(p, (c * 7 + b) * 7 + a, row + o.x[6 - a]);
+                const int i = (c * 7 + b) * 7 + a;
+                const ST v = __ldg(p.src + ((uint64_t)i * (uint64_t)p.S + (uint64_t)(uint32_t)(row + o.x[6 - a])));
+                if constexpr (KEEP) stash[i * kBlockX + threadIdx.x] = v;
+                const float g = decode_pop(p, i, v);
                 cs[a] += g;
                 rsum += g;
             }
@@ -61,6 +96,10 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
             jz = fmaf(dc, rsum, jz);
             e2yz = fmaf(db * db + dc * dc, rsum, e2yz);
         }
+    };
+    for (int c = 0; c < 7; ++c) {
+        if (c < NS) plane1(std::true_type{}, c);
+        else plane1(std::false_type{}, c);
     }
     float jx = 0.f, e2 = e2yz;
 #pragma unroll
@@ -91,7 +130,8 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
     // The correction sums are accumulated per row of 7 and then per plane, so
     // each carries the rounding of ~2 x 7 additions rather than of 343.
     // Planes in reverse order (see above).
-    for (int c = 6; c >= 0; --c) {
+    auto plane2 = [&](auto kept, int c) {
+        constexpr bool KEPT = decltype(kept)::value;
         const int zo = bc_wrap(z - (c - 3), p.Z, p.bc2) * plane;
         const int ez = c - 3;
         float p0 = 0.f, p2 = 0.f, px = 0.f, py = 0.f;  // plane sums
@@ -112,7 +152,9 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
                 r0 += q;
                 r2 = fmaf((float)E2, q, r2);
                 if (ex) rx = fmaf((float)ex, q, rx);
-                const float g = ld(p, i, row + o.x[6 - a]);
+                float g;
+                if constexpr (KEPT) g = decode_pop(p, i, stash[i * kBlockX + threadIdx.x]);
+                else g = ld(p, i, row + o.x[6 - a]);
                 if (E2 <= 1) {  // the rest and the six unit velocities: stored last
                     if (E2 == 0) { q_c = q; g_c = g; }
                     else if (ex == -1) { q_mx = q; g_mx = g; }
@@ -135,6 +177,10 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
         ax += px;
         ay += py;
         az = fmaf((float)ez, p0, az);
+    };
+    for (int c = 6; c >= 0; --c) {
+        if (c < NS) plane2(std::true_type{}, c);
+        else plane2(std::false_type{}, c);
     }
     const float d0 = om_rho - acc0;
     const float d2 = p.omega * m.E2_eq - acc2;
@@ -163,7 +209,15 @@ template <bool ROT, typename ST> cudaError_t launch_step_q343(const Args &a, cud
 {
     const auto p = make_params<kQ343, ST>(a);
     const dim3 grid((a.X + kBlockX - 1) / kBlockX, a.Y, a.Z);
-    k_step_q343<ROT, ST><<<grid, kBlockX, 0, s>>>(p);
+    constexpr size_t sh = stash_bytes<ST>();
+    static bool attr = false;
+    if (!attr && sh > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_step_q343<ROT, ST>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_step_q343<ROT, ST><<<grid, kBlockX, sh, s>>>(p);
     return cudaGetLastError();
 }
 
