@@ -422,7 +422,9 @@ int lbm_nn_apply(const float *rho, const float *u, const float *T, const float *
  * a state (rho, u, T) and a second state (rho2, u2, T2):
  *   residual[b] (may be NULL) = max of the relative changes of the totals of
  *     mass, momentum (relative to the mass) and energy
- *     rho ((1+n)/2 T + u^2/2), half_dof[b] = (1+n)/2;
+ *     rho ((1+n)/2 T + u^2/2), half_dof[b] = (1+n)/2; +infinity if the
+ *     second state has a non-positive or non-finite rho or T, or a
+ *     non-finite u, anywhere in the window;
  *   l1[b] (may be NULL) = max over rho, u, T of sum|first - second| over
  *     the window divided by sum|rho2|, sum sqrt(gamma T2) and sum|T2|
  *     (the second state is the reference);

@@ -1417,10 +1417,13 @@ __global__ void k_tube_checks(const float *rho, const float *u, const float *T, 
     float s[NV] = {};
     float bv = -1.0f;
     int bi = w0;
+    int unphysical = 0;  // a non-positive or non-finite rho or T in the second state
     for (int l = w0 + threadIdx.x; l < w0 + W; l += blockDim.x) {
         const int64_t i = (int64_t)b * L + l;
         const float r1 = rho[i], v1 = u[i], t1 = T[i], r2 = rho2[i], v2 = u2[i], t2 = T2[i];
         if (residual) {
+            unphysical |= !(r2 > 0.f) || !(t2 > 0.f) || !(r2 < INFINITY) || !(t2 < INFINITY) ||
+                          !isfinite(v2);
             const float j1 = r1 * v1;
             const float e1 = r1 * fmaf(cv, t1, 0.5f * v1 * v1);
             s[0] += r1;
@@ -1445,6 +1448,7 @@ __global__ void k_tube_checks(const float *rho, const float *u, const float *T, 
         }
     }
     // one block-wide reduction of all the sums
+    unphysical = __syncthreads_or(unphysical);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
@@ -1481,7 +1485,7 @@ __global__ void k_tube_checks(const float *rho, const float *u, const float *T, 
             const double m = fabs(tot[3]) / tot[0];
             const double j = fabs(tot[4]) / tot[0];
             const double e = fabs(tot[5]) / tot[2];
-            residual[b] = (float)fmax(m, fmax(j, e));
+            residual[b] = unphysical ? INFINITY : (float)fmax(m, fmax(j, e));
         }
         if (l1) {
             const double er = tot[6] / tot[11];

@@ -265,6 +265,16 @@ def test_data_kernels(lbmlib):
         assert host(starts)[b] == st and host(starts)[B + b] == st + 4
     r32 = [np.float32(v).astype(np.float64) for v in (rho, u, T, rho2, u2, T2)]
     np.testing.assert_allclose(host(res), S.conservation_residual(*r32, n), rtol=1e-5)
+    # a non-positive T anywhere in the second state fails the residual check
+    T2bad = np.float32(T2).copy()
+    T2bad[1, L // 3] = -1e-3
+    g2b = [g2[0], g2[1], f32(T2bad).reshape(-1)]
+    res2 = torch.empty(B, dtype=torch.float32, device="cuda")
+    assert net.lib.lbm_nn_tube_checks(*(vp(x) for x in g + g2b), vp(hd), None, vp(res2), None,
+                                      None, 0, 0, B, L, 0, L, stream()) == 0
+    r2h = host(res2)
+    assert np.isinf(r2h[1]) and np.all(np.isfinite(r2h[[0, 2]]))
+    np.testing.assert_allclose(r2h[[0, 2]], host(res)[[0, 2]], rtol=1e-6)
     np.testing.assert_allclose(host(l1), S.l1_error(*r32[:3], *r32[3:], np.float32(gam)),
                                rtol=1e-5)
 
