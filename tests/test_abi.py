@@ -113,5 +113,13 @@ def test_batch_create_validation_and_sizes(lbmlib):
         assert lbmlib.lbm_batch_set_block(h, 100, 0) == -1
         assert lbmlib.lbm_batch_set_block(h, 512, -1) == -1
         assert lbmlib.lbm_batch_set_block(h, 512, 2) == 0
+        # watch ranges: 0 <= lo <= hi <= length per problem, both or neither
+        IA = ctypes.c_int * 3
+        assert lbmlib.lbm_batch_set_watch(h, IA(0, 5, 10), IA(10, 35, 33)) == 0
+        assert lbmlib.lbm_batch_set_watch(h, IA(0, 5, 10), IA(11, 35, 33)) == -1  # hi > length
+        assert lbmlib.lbm_batch_set_watch(h, IA(0, 6, 10), IA(10, 5, 33)) == -1   # lo > hi
+        assert lbmlib.lbm_batch_set_watch(h, IA(-1, 0, 0), IA(10, 40, 33)) == -1  # lo < 0
+        assert lbmlib.lbm_batch_set_watch(h, IA(0, 0, 0), None) == -1            # one of two
+        assert lbmlib.lbm_batch_set_watch(h, None, None) == 0                   # whole problems
     finally:
         lbmlib.lbm_batch_destroy(h)
