@@ -8,6 +8,9 @@
 // L2-coherent path because the launch reads back what it wrote one step
 // earlier.  A problem of L nodes keeps 2 x 14 x L floats live, so the
 // resident problems (a few hundred) stay in the 126 MB L2 for their whole run.
+// When the longest problem has at most 864 nodes, a second form keeps each
+// problem's two buffers in shared memory for the whole run (k_batch_run_sm).
+// A per-problem watch range limits which nodes may set its status word.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
