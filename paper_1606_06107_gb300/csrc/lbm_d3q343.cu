@@ -13,6 +13,8 @@
 // velocities are stored last with the float32 moment corrections, as in the
 // one- and two-dimensional kernels.  Element indices are 64-bit (the state
 // of a 384^3 grid holds 2 x 10^10 values).
+#include <atomic>
+
 #include "lbm_step.cuh"
 
 namespace lbm {
@@ -210,12 +212,18 @@ template <bool ROT, typename ST> cudaError_t launch_step_q343(const Args &a, cud
     const auto p = make_params<kQ343, ST>(a);
     const dim3 grid((a.X + kBlockX - 1) / kBlockX, a.Y, a.Z);
     constexpr size_t sh = stash_bytes<ST>();
-    static bool attr = false;
-    if (!attr && sh > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_step_q343<ROT, ST>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if constexpr (sh > 48 * 1024) {  // the opt-in limit is a per-device function attribute
+        static std::atomic<bool> done[64];
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
-        attr = true;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!done[dev].load()) {
+            e = cudaFuncSetAttribute(k_step_q343<ROT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sh);
+            if (e != cudaSuccess) return e;
+            done[dev].store(true);
+        }
     }
     k_step_q343<ROT, ST><<<grid, kBlockX, sh, s>>>(p);
     return cudaGetLastError();
