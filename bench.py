@@ -545,6 +545,67 @@ def dist_setup(n_gpus):
     return world, rank, local
 
 
+def blast_storage_crop(dev, L: int = 384, steps: int = 500, crop: int = 64, n: int = 0,
+                       chunk: int = 0):
+    """Storage error of the 3-D blast: the same L^3 problem run with f16
+    deviation storage and with float storage (2 x 79 GB of state), compared
+    on the central crop^3 nodes (rel-L1 of rho, T and of u against the
+    sound-speed scale).  Both run in chunks of `chunk` steps up to `steps`;
+    each records the last chunk after which its status word is still clear,
+    and the crops are compared at the last step both reached finite."""
+    import torch
+
+    from paper_1606_06107_gb300 import Lbm, workloads
+
+    c0 = L // 2 - crop // 2
+    sl = slice(c0, c0 + crop)
+    chunk = chunk or max(1, steps // 10)
+    crops, out = {}, {}
+    for storage in ("f16", "f32"):
+        wl = workloads.blast_3d(L=L, radius=32 * L / 384, n=n, p_in=1.5, p_out=0.5)
+        g = Lbm("D3Q343", n, 2 / 3, (L, L, L), ("periodic",) * 3, device=dev, storage=storage)
+        g.set_macro(wl.rho, wl.u, wl.T)
+        del wl
+        crops[storage] = {}
+        done, ms = 0, 0.0
+        while done < steps:
+            k = min(chunk, steps - done)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.step(k)
+            b.record()
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+            done += k
+            if g.status() != 0:
+                break
+            rho, u, T = g.moments()
+            crops[storage][done] = (rho.view(L, L, L)[sl, sl, sl].double().cpu().numpy(),
+                                    u.view(3, L, L, L)[:, sl, sl, sl].double().cpu().numpy(),
+                                    T.view(L, L, L)[sl, sl, sl].double().cpu().numpy())
+            del rho, u, T
+        last = max(crops[storage] or [0])
+        out[storage] = {"ms_per_step": ms / done, "finite_through_step": last,
+                        "status_set_by_step": done if last < done else None,
+                        "state_GB_two_buffers": 2 * g.state_bytes / 1e9}
+        del g
+        torch.cuda.empty_cache()
+    common = sorted(set(crops["f16"]) & set(crops["f32"]))
+    out["rel_l1_f16_vs_f32"] = {}
+    for at in common:
+        (r16, u16, t16), (r32, u32, t32) = crops["f16"][at], crops["f32"][at]
+        cs = np.sqrt((3 + n + 2) / (3 + n) * t32)
+        out["rel_l1_f16_vs_f32"][str(at)] = {
+            "rho": float(np.abs(r16 - r32).sum() / np.abs(r32).sum()),
+            "u": float(np.abs(u16 - u32).sum() / (3 * cs.sum())),
+            "T": float(np.abs(t16 - t32).sum() / np.abs(t32).sum())}
+    out["config"] = (f"blast_3d {L}^3 D3Q343 n={n}, stable-envelope variant p 1.5 | 0.5, "
+                     f"up to {steps} steps in chunks of {chunk}, central {crop}^3 crop")
+    return out
+
+
 def max_over_ranks(x: float, world: int, device) -> float:
     """The largest of the ranks' values (the job's wall time is the slowest
     replica's); the identity on one rank."""
@@ -625,6 +686,10 @@ def run_gpu(args):
         else:
             res = blast_leg(dev, L=args.blast_size, steps=args.blast_steps,
                             oracle_L=min(16, args.blast_size), oracle_steps=5)
+            if args.blast_crop_steps > 0:
+                res["storage_error_crop"] = blast_storage_crop(dev, L=args.blast_size,
+                                                               steps=args.blast_crop_steps,
+                                                               crop=min(64, args.blast_size))
         print(json.dumps(res), flush=True)
         return
     if world > 1:
@@ -781,6 +846,9 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=4000)
     ap.add_argument("--blast-size", type=int, default=384)
     ap.add_argument("--blast-steps", type=int, default=10)
+    ap.add_argument("--blast-crop-steps", type=int, default=0,
+                    help="with --only blast: also run the problem with f16 and with float "
+                         "storage for this many steps and compare the central 64^3 crop")
     ap.add_argument("--size", type=int, default=X, help="grid edge (profiling of smaller cases)")
     args = ap.parse_args()
     if args.warmup < 3:
