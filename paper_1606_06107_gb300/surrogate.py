@@ -502,6 +502,23 @@ def cosine_lr(step, total, peak=1e-3, warmup=100, floor=0.02):
 
 
 # ------------------------------------------------------------------ runtime
+def fallback_windows(L: int, width: int, margin: int):
+    """Windows that recompute a tube of L nodes exactly: interiors of `width`
+    nodes tile [0, L) (the last one moved back to end at L, overlapping its
+    neighbour), each inside a window of S = width + 2 margin nodes placed so
+    that every interior node is at least `margin` nodes from a window edge
+    that is not a tube end.  Returns (S, interior starts, window starts);
+    one window, the whole tube, when L <= S."""
+    width = max(1, min(int(width), L))
+    S = min(L, width + 2 * margin)
+    if S == L:
+        return L, np.zeros(1, np.int64), np.zeros(1, np.int64)
+    nw = -(-L // width)
+    istart = np.minimum(np.arange(nw, dtype=np.int64) * width, L - width)
+    wstart = np.clip(istart - margin, 0, L - S)
+    return S, istart, wstart
+
+
 def _latency_block(length: int) -> int:
     """Block size of an ensemble run whose time is one problem's latency (a
     few problems, or one wave of short ones): one node per thread, up to
@@ -638,15 +655,9 @@ class SurrogateRunner:
         run fails; a tube on which any window fails keeps its prediction and
         is quarantined."""
         t, net, lib = self.torch, self.net, self.net.lib
-        L, M = self.L, self.margin
-        Wi = self.fb_window
-        S = min(L, Wi + 2 * M)
-        if S == L:  # one window: the whole tube
-            Wi, istart, wstart = L, np.zeros(1, np.int64), np.zeros(1, np.int64)
-        else:
-            nw = -(-L // Wi)
-            istart = np.minimum(np.arange(nw) * Wi, L - Wi)     # the last one may overlap
-            wstart = np.clip(istart - M, 0, L - S)
+        L = self.L
+        S, istart, wstart = fallback_windows(L, self.fb_window, self.margin)
+        Wi = L if S == L else min(self.fb_window, L)
         nw = istart.size
         f = len(tubes)
         count = f * nw
