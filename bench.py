@@ -138,6 +138,55 @@ def cpu_oracle_rate(seconds: float = 12.0, size: int = REF_SAMPLE, max_steps: in
     return size * size * steps / dt / 1e6, steps, dt, threads
 
 
+def oracle_timing(budget: float = 8.0):
+    """The FP64 oracle's throughput (Mnode-updates/s) on each workload, on
+    the host threads this process runs with (OMP_NUM_THREADS, default all
+    cores), each on a sample bounded by about `budget` seconds:
+    Sod 1-D in full (1000 nodes, 2000 steps), the 2-D Riemann problem at
+    256^2, the 3-D blast at its 64^3 scaled variant (n = 0), and 64 tubes of
+    the ensemble workload (FD transport, m = 10)."""
+    import platform
+
+    from oracle import oracle
+    from paper_1606_06107_gb300 import workloads
+
+    def timed(sims, nodes, max_steps):
+        for sim in sims:
+            sim.step(1)  # warm-up (page-in, thread pool)
+        steps, t0 = 0, time.perf_counter()
+        while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < budget):
+            for sim in sims:
+                sim.step(1)
+            steps += 1
+        dt = time.perf_counter() - t0
+        return {"value": nodes * steps / dt / 1e6, "steps": steps, "seconds": dt}
+
+    out = {}
+    wl = workloads.sod_1d(1000)
+    sim = oracle.Sim(oracle.D1Q7, wl.n, wl.tau, wl.shape, (oracle.COPY,))
+    sim.set_macro(wl.rho, wl.u, wl.T)
+    out["sod_1d 1000 nodes, 2000 steps"] = timed([sim], 1000, 2000)
+    wl = workloads.riemann_2d(256, 256, seed=0, mild=True)
+    sim = oracle.Sim(oracle.D2Q49, wl.n, wl.tau, wl.shape, (oracle.PERIODIC,) * 2)
+    sim.set_macro(wl.rho, wl.u, wl.T)
+    out["riemann_2d_mild 256^2 D2Q49, up to 200 steps"] = timed([sim], 256 * 256, 200)
+    wl = workloads.blast_3d(L=64, radius=32 * 64 / 384, n=0, p_in=1.5, p_out=0.5)
+    sim = oracle.Sim(oracle.D3Q343, 0, wl.tau, wl.shape, (oracle.PERIODIC,) * 3)
+    sim.set_macro(wl.rho, wl.u, wl.T)
+    out["blast_3d 64^3 D3Q343 n=0"] = timed([sim], 64 ** 3, 10 ** 9)
+    tubes = workloads.batched_tubes(count=64, seed=0)
+    sims = []
+    for w in tubes:
+        sim = oracle.Sim(oracle.D1Q7, w.n, w.tau, w.shape, (oracle.COPY,), mode=oracle.FD,
+                         m_fd=10)
+        sim.set_macro(w.rho, w.u, w.T)
+        sims.append(sim)
+    out["64 ensemble tubes, FD m=10"] = timed(sims, sum(w.shape[0] for w in tubes), 10 ** 9)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"kind": "oracle", "unit": "Mnode-updates/s", "threads": threads,
+            "host": f"{platform.machine()}, {os.cpu_count()} cores", "workloads": out}
+
+
 def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
                 sample_steps: int = 200):
     """The ensemble workload: `count` 1-D shock tubes of uneven length
@@ -830,6 +879,8 @@ def main():
                     help="use the stated quadrant draws (goes non-finite) instead of the "
                          "stable-envelope variant")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="time the FP64 oracle on every workload on the host and exit")
     ap.add_argument("--no-batched", action="store_true", help="skip the ensemble leg")
     ap.add_argument("--no-blast", action="store_true", help="skip the 3-D D3Q343 leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
@@ -853,6 +904,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.oracle_timing:
+        print(json.dumps(oracle_timing()), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
