@@ -147,7 +147,9 @@ int lbm_conservation(lbm_handle h, double *out);
  * on every GPU that loads the library until the process exits); nothing is
  * allocated.
  *   state  device pointer to one state buffer in the layout lbm_set_grid
- *          describes (256-byte aligned), on the current device.  For a bound
+ *          describes (256-byte aligned), device or managed memory of the
+ *          current device (checked on the host with
+ *          cudaPointerGetAttributes; anything else is LBM_EINVAL).  For a bound
  *          handle, the current state is buf_a after an even number of steps
  *          since lbm_set_macro / lbm_set_state and buf_b after an odd number.
  *   stream cudaStream_t the work is enqueued on (NULL = legacy default).
@@ -155,7 +157,10 @@ int lbm_conservation(lbm_handle h, double *out);
  * Needs lbm_set_grid, not lbm_bind; does not read the sticky status flag.
  * Synchronizing (waits for `stream`).  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * current, and keeps it for the life of the process; after a cudaDeviceReset
+ * of that device the kept address is stale, so do not call this entry point
+ * on a device that was reset in the same process.  Make the first call on a
+ * device before any stream capture.  All calls share
  * the one array: calls that overlap on the GPU (different streams or host
  * threads, same device) race and may return wrong sums.  Returns LBM_ESIZE if
  * the reduction would need more than the array's 1024 block records (more

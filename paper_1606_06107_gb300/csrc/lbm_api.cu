@@ -649,7 +649,9 @@ std::mutex g_noalloc_mu;
 double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device, looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached for the life of the
+// process.  A cudaDeviceReset destroys the context the address belongs to,
+// so the cache is not valid across one (the header says so).
 cudaError_t noalloc_scratch(int dev, double **out)
 {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -675,6 +677,18 @@ extern "C" int lbm_conservation_noalloc(lbm_handle h, const void *state, void *s
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(h, LBM_EINVAL, "device ordinal too large");
+    // The state must be device (or managed) memory of the current device: a
+    // host pointer or another GPU's buffer would make the reduction kernel
+    // fault.  This query reads only the driver's host-side records.
+    cudaPointerAttributes attr{};
+    e = cudaPointerGetAttributes(&attr, state);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear the (non-sticky) error this query left behind
+        return fail(h, LBM_EINVAL, "state is not a CUDA device pointer");
+    }
+    if ((attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) ||
+        attr.device != dev)
+        return fail(h, LBM_EINVAL, "state must be device memory of the current device");
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceGetAttribute");
