@@ -698,9 +698,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        # the workload of the measured arm; each step runs a bounded sample of it
-        "config": {"workload": f"{wl.name} {X}x{Y} {LATTICE}+D1Q7 n={NROT} tau=2/3 periodic "
-                               f"STREAM, seed=rank", "nodes_per_gpu": X * Y,
+        # the grid actually run: a bounded sample of the measured arm's
+        # 2048 x 2048 problem (same recipe, seed and physics), per node-update
+        "config": {"workload": f"{wl.name} {side}x{side} {LATTICE}+D1Q7 n={NROT} tau=2/3 "
+                               f"periodic STREAM, seed=0 (sample of the {X}x{Y} workload)",
+                   "nodes_per_gpu": side * side, "sample_of": f"{X}x{Y}",
                    "bytes_per_node_step": BYTES_PER_NODE, "parallelism": "replicas x1"},
         "cpu_baseline": {"value": value, "unit": "Mnode-updates/s", "cores": threads,
                          "kind": "oracle",
