@@ -587,6 +587,59 @@ def blast_leg(dev, L: int = 384, steps: int = 10, storage: str = "f16", oracle_L
     return out
 
 
+def storage_leg(dev, size: int = 2048, steps: int = 300, storages=("f32", "f16", "bf16"),
+                oracle_size: int = 256, oracle_steps: int = 100):
+    """The main 2-D workload (riemann_2d_mild, D2Q49 + D1Q7, STREAM) with each
+    population storage: time per fused step at size^2 (CUDA events around
+    `steps` launches after 3 warm-up steps) and the algorithmic bandwidth at
+    that storage's bytes per node-step; and the rel-L1 error in rho, u, T
+    against the FP64 oracle on the same recipe at oracle_size^2 after
+    oracle_steps steps (same seed)."""
+    import torch
+
+    from oracle import oracle
+    from paper_1606_06107_gb300 import Lbm, workloads
+
+    hbm, _ = peaks()
+    wl = workloads.riemann_2d(size, size, seed=0, mild=True)
+    ws = workloads.riemann_2d(oracle_size, oracle_size, seed=0, mild=True)
+    ref = oracle.Sim(oracle.D2Q49, ws.n, ws.tau, ws.shape, (oracle.PERIODIC,) * 2)
+    ref.set_macro(ws.rho, ws.u, ws.T)
+    ref.step(oracle_steps)
+    ref_m = ref.moments()
+    out = {"workload": f"{wl.name} {size}x{size} {LATTICE}+D1Q7 n={NROT} STREAM",
+           "error_sample": f"{ws.name} {oracle_size}x{oracle_size}, {oracle_steps} steps, "
+                           f"vs FP64 oracle"}
+    for st in storages:
+        g = Lbm(LATTICE, NROT, TAU, (size, size), ("periodic",) * 2, device=dev, storage=st)
+        g.set_macro(wl.rho, wl.u, wl.T)
+        g.step(3)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.step(steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        status = g.status()
+        bpn = (QT + QR) * 2 * (4 if st == "f32" else 2)
+        gbs = size * size * bpn / (ms * 1e-3) / 1e9
+        del g
+        torch.cuda.empty_cache()
+        s = Lbm(LATTICE, NROT, TAU, ws.shape, ("periodic",) * 2, device=dev, storage=st)
+        s.set_macro(ws.rho, ws.u, ws.T)
+        s.step(oracle_steps)
+        errs = [float(np.abs(x.cpu().numpy().astype(np.float64).reshape(y.shape) - y).sum()
+                      / np.abs(y).sum()) for x, y in zip(s.moments(), ref_m)]
+        out[st] = {"ms_per_step": ms, "value": size * size / ms / 1e3,
+                   "unit": "Mnode-updates/s", "bytes_per_node_step": bpn,
+                   "algorithmic_GBps": gbs, "frac_of_hbm": gbs / hbm, "status": status,
+                   "rel_l1_vs_fp64_oracle": {"rho": errs[0], "u": errs[1], "T": errs[2]}}
+        del s
+    return out
+
+
 def dist_setup(n_gpus):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -734,6 +787,9 @@ def run_gpu(args):
                                 windows=args.surrogate_windows,
                                 train_seconds=args.surrogate_seconds, patch=args.surrogate_patch)
             add_peak(res["roofline"])
+        elif args.only == "storage":
+            res = storage_leg(dev, size=args.size, steps=args.storage_steps,
+                              storages=tuple(args.storages.split(",")))
         else:
             res = blast_leg(dev, L=args.blast_size, steps=args.blast_steps,
                             oracle_L=min(16, args.blast_size), oracle_steps=5)
@@ -826,6 +882,10 @@ def run_gpu(args):
     batched = None
     if world == 1 and not args.no_batched:
         batched = batched_leg(dev, steps=args.batched_steps, count=args.batched_count)
+    storage = None
+    if world == 1 and not args.no_storage:
+        storage = storage_leg(dev, size=X, steps=args.storage_steps,
+                              storages=tuple(args.storages.split(",")))
     blast = None
     if world == 1 and not args.no_blast:
         blast = blast_leg(dev, L=args.blast_size, steps=args.blast_steps)
@@ -862,6 +922,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "batched": batched,
+        "storage": storage,
         "blast_3d": blast,
         "surrogate": surrogate,
     }
@@ -886,7 +947,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the ensemble leg")
     ap.add_argument("--no-blast", action="store_true", help="skip the 3-D D3Q343 leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
-    ap.add_argument("--only", default="all", choices=["all", "batched", "blast", "surrogate", "conv"],
+    ap.add_argument("--only", default="all", choices=["all", "batched", "blast", "surrogate", "conv",
+                                                     "storage"],
                     help="run one leg alone (profiling)")
     ap.add_argument("--surrogate-train-tubes", type=int, default=1600)
     ap.add_argument("--surrogate-eval-tubes", type=int, default=1024)
@@ -903,6 +965,10 @@ def main():
                     help="with --only blast: also run the problem with f16 and with float "
                          "storage for this many steps and compare the central 64^3 crop")
     ap.add_argument("--size", type=int, default=X, help="grid edge (profiling of smaller cases)")
+    ap.add_argument("--storage-steps", type=int, default=300)
+    ap.add_argument("--storages", default="f32,f16,bf16",
+                    help="storages for the storage leg (include/lbm.h lbm_set_storage)")
+    ap.add_argument("--no-storage", action="store_true", help="skip the storage leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -342,12 +342,22 @@ __device__ __forceinline__ Moments make_moments(const Params<Q, ST> &p, float rh
     // the total energy, by the same ~1e-8 every step.
     const float jj = (jx * jx + jy * jy + jz * jz) * inv_rho;  // rho u^2 / r^2
     if constexpr (sizeof(ST) < sizeof(float)) {
-        // reduced-precision storage: the temperature is recovered from the
-        // total energy in double precision (e2 - jj cancels at high Mach)
-        const double rd = (double)rho;
-        const double jjd = ((double)jx * jx + (double)jy * jy + (double)jz * jz) / rd;
-        const double num = 0.5 * ((double)e2 - jjd) / rd + (ROT ? (double)p.half_n * R2 : 0.0);
-        m.T_lat = (float)(num / (double)p.cT);
+        // Reduced-precision storage: the temperature is recovered from the
+        // total energy with the kinetic part subtracted in double precision,
+        // where e2 - |j|^2 / rho cancels at high Mach.  Only that difference
+        // needs double: |j|^2 of float components is exact in double, 1/rho
+        // is the float reciprocal refined by one Newton step (relative error
+        // ~1e-14), and the difference is formed by one fused multiply-add.
+        // Everything after the cancellation keeps float's relative accuracy.
+        // (GB300's FP64 pipe is slow: three double divisions per node held
+        // the 16-bit step kernels to 56 % FP64-pipe utilisation.)
+        double jjd = (double)jx * (double)jx;
+        if (D >= 2) jjd = fma((double)jy, (double)jy, jjd);
+        if (D >= 3) jjd = fma((double)jz, (double)jz, jjd);
+        const double r0 = (double)inv_rho;
+        const double inv_rho_d = fma(r0, fma(-(double)rho, r0, 1.0), r0);
+        const float th = (float)fma(-jjd, inv_rho_d, (double)e2);  // 2 (K - rho u^2/2) / r^2
+        m.T_lat = __fdiv_rn(0.5f * th * inv_rho + (ROT ? p.half_n * R2 : 0.f), p.cT);
     } else {
         m.T_lat = __fdiv_rn(0.5f * (e2 - jj) * inv_rho + (ROT ? p.half_n * R2 : 0.f), p.cT);
     }
