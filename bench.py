@@ -587,7 +587,8 @@ def blast_leg(dev, L: int = 384, steps: int = 10, storage: str = "f16", oracle_L
     return out
 
 
-def storage_leg(dev, size: int = 2048, steps: int = 300, storages=("f32", "f16", "bf16"),
+def storage_leg(dev, size: int = 2048, steps: int = 300,
+                storages=("f32", "f16", "bf16", "f16_node", "bf16_node"),
                 oracle_size: int = 256, oracle_steps: int = 100):
     """The main 2-D workload (riemann_2d_mild, D2Q49 + D1Q7, STREAM) with each
     population storage: time per fused step at size^2 (CUDA events around
@@ -623,7 +624,9 @@ def storage_leg(dev, size: int = 2048, steps: int = 300, storages=("f32", "f16",
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
         status = g.status()
-        bpn = (QT + QR) * 2 * (4 if st == "f32" else 2)
+        # every population read and written once; per-node reference storage
+        # adds its 16-byte record per node, read once and written once
+        bpn = (QT + QR) * 2 * (4 if st == "f32" else 2) + (32 if st.endswith("_node") else 0)
         gbs = size * size * bpn / (ms * 1e-3) / 1e9
         del g
         torch.cuda.empty_cache()
@@ -966,7 +969,7 @@ def main():
                          "storage for this many steps and compare the central 64^3 crop")
     ap.add_argument("--size", type=int, default=X, help="grid edge (profiling of smaller cases)")
     ap.add_argument("--storage-steps", type=int, default=300)
-    ap.add_argument("--storages", default="f32,f16,bf16",
+    ap.add_argument("--storages", default="f32,f16,bf16,f16_node,bf16_node",
                     help="storages for the storage leg (include/lbm.h lbm_set_storage)")
     ap.add_argument("--no-storage", action="store_true", help="skip the storage leg")
     args = ap.parse_args()

@@ -95,10 +95,34 @@ int lbm_set_mode(lbm_handle h, int mode, int m_fd);
  * (default) keeps float32 values.  LBM_STORE_F16 / LBM_STORE_BF16 keep the
  * relative deviation from the rest equilibrium, d_i = f_i / w_i - 1, as IEEE
  * half / bfloat16, halving the bytes per step; all arithmetic stays float32
- * and the temperature is recovered from the total energy in double
- * precision (Eq. T).  The reduced precision changes results by the storage
- * rounding (about 2^-11 resp. 2^-8 of d_i per step). */
-enum lbm_storage { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2 };
+ * and the temperature is recovered from the total energy with its kinetic
+ * part subtracted in double precision (Eq. T).  The reduced precision
+ * changes results by the storage rounding (about 2^-11 resp. 2^-8 of d_i
+ * per step).
+ *
+ * LBM_STORE_F16_NODE / LBM_STORE_BF16_NODE keep the deviation from a
+ * per-node reference equilibrium instead, so the 16 bits resolve the
+ * departure from the node's own local equilibrium rather than from rest.
+ * Each node stores a reference record of four floats after the populations
+ * (16 bytes per node, 14 % more bytes per step on D2Q49 + D1Q7):
+ * (rho - 1, rho (T - 1) / 2, rho r u_x, rho r u_y) of the moments at which
+ * the node last collided (set_macro: the initial fields; set_state: rest).  A
+ * translational value is stored as s_i = f_i / w_i - R_i with the
+ * first-order Hermite terms of the equilibrium of Sec. IV,
+ * R_i = rho (1 + xi_i.u + (T - 1)(|xi_i|^2 - D) / 2), and a rotational value
+ * as s_j = h_j / w_j - h_j^eq(T) / w_j (its full equilibrium, which depends
+ * on T only); a pulled value is decoded with the record of the node it was
+ * pulled from.  Writer and reader evaluate R from the same stored floats
+ * with the same fused operations, so the reference cancels exactly.
+ * LBM_MODE_STREAM and the 1-D and 2-D lattices only (lbm_set_grid returns
+ * LBM_EINVAL otherwise). */
+enum lbm_storage {
+    LBM_STORE_F32 = 0,
+    LBM_STORE_F16 = 1,
+    LBM_STORE_BF16 = 2,
+    LBM_STORE_F16_NODE = 3,
+    LBM_STORE_BF16_NODE = 4
+};
 int lbm_set_storage(lbm_handle h, int storage);
 
 /* Set the grid: shape[0..D-1] = X (fastest), Y, Z, each >= 1 (Y, Z <= 65535);

@@ -30,7 +30,7 @@ struct lbm_ctx {
     int bc[3] = {0, 0, 0};
     int pitch = 0;
     int64_t S = 0, N = 0;
-    size_t state_bytes = 0, work_bytes = 0;
+    size_t state_bytes = 0, work_bytes = 0, ref_offset = 0;
     bool grid_set = false, bound = false, has_state = false;
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;
@@ -250,6 +250,7 @@ Args make_args(const lbm_ctx *h)
     a.mode = h->mode;
     a.m_fd = h->m_fd;
     a.storage = h->storage;
+    a.ref_offset = h->ref_offset;
     a.X = (int)h->shape[0];
     a.Y = (int)h->shape[1];
     a.Z = (int)h->shape[2];
@@ -374,7 +375,7 @@ int lbm_set_storage(lbm_handle h, int storage)
 {
     if (!h) return LBM_EINVAL;
     if (h->grid_set) return fail(h, LBM_ESTATE, "lbm_set_storage must precede lbm_set_grid");
-    if (storage != LBM_STORE_F32 && storage != LBM_STORE_F16 && storage != LBM_STORE_BF16)
+    if (storage < LBM_STORE_F32 || storage > LBM_STORE_BF16_NODE)
         return fail(h, LBM_EINVAL, "unknown storage");
     h->storage = storage;
     return LBM_OK;
@@ -409,6 +410,9 @@ int lbm_set_grid(lbm_handle h, const int64_t *shape, const int *bc, size_t *stat
     }
     if (s[0] > (int64_t)1 << 30 || s[1] > 65535 || s[2] > 65535)
         return fail(h, LBM_ESIZE, "X <= 2^30 and Y, Z <= 65535 are required");
+    const bool node_ref = h->storage == LBM_STORE_F16_NODE || h->storage == LBM_STORE_BF16_NODE;
+    if (node_ref && (h->lattice == LBM_D3Q343 || h->mode != LBM_MODE_STREAM))
+        return fail(h, LBM_EINVAL, "per-node reference storage needs STREAM mode and a 1-D or 2-D lattice");
     const size_t elem = (h->storage == LBM_STORE_F32) ? sizeof(float) : 2;
     const int64_t row_align = 128 / (int64_t)elem;  // rows start on 128-byte lines
     const int64_t pitch = (s[0] + row_align - 1) / row_align * row_align;
@@ -426,6 +430,11 @@ int lbm_set_grid(lbm_handle h, const int64_t *shape, const int *bc, size_t *stat
     h->S = S;
     h->N = s[0] * s[1] * s[2];
     h->state_bytes = elem * (size_t)(h->Q + h->Qr) * (size_t)S;
+    h->ref_offset = 0;
+    if (node_ref) {  // the reference records follow the populations, 256-byte aligned
+        h->ref_offset = (h->state_bytes + 255) / 256 * 256;
+        h->state_bytes = h->ref_offset + 16 * (size_t)S;
+    }
     h->work_bytes = lbm::kWorkBytes;
     h->grid_set = true;
     if (state_bytes) *state_bytes = h->state_bytes;

@@ -22,7 +22,10 @@ enum class Op { Step, Init, Moments, Conserve, GetState, SetState, Sample };
 // Everything a kernel launch needs; filled by the host API.
 struct Args {
     int lattice, D, Q, Qr, mode, m_fd;
-    int storage;  // lbm_storage: 0 float, 1 half deviations, 2 bfloat16 deviations
+    int storage;  // lbm_storage: 0 float, 1 half / 2 bfloat16 deviations from rest,
+                  // 3 half / 4 bfloat16 deviations from a per-node reference
+    size_t ref_offset;  // storage 3, 4: bytes from a state buffer's start to its
+                        // per-node reference records (float4 per node, S of them)
     int X, Y, Z, pitch;
     int64_t S;  // population stride in floats (pitch * Y * Z)
     int64_t N;  // nodes (X * Y * Z)

@@ -129,6 +129,7 @@ template <typename ST> struct Storage;
 template <> struct Storage<__half> {
     __device__ static float decode(__half v, float w) { return fmaf(w, __half2float(v), w); }
     __device__ static __half encode(float f, float inv_w) { return __float2half_rn(fmaf(f, inv_w, -1.0f)); }
+    __device__ static __half from_dev(float d) { return __float2half_rn(d); }
 };
 template <> struct Storage<__nv_bfloat16> {
     __device__ static float decode(__nv_bfloat16 v, float w)
@@ -139,6 +140,7 @@ template <> struct Storage<__nv_bfloat16> {
     {
         return __float2bfloat16_rn(fmaf(f, inv_w, -1.0f));
     }
+    __device__ static __nv_bfloat16 from_dev(float d) { return __float2bfloat16_rn(d); }
 };
 
 // ---------------------------------------------------------------------------
@@ -160,7 +162,47 @@ template <int Q, typename ST = float> struct Params {
     float r, r2, inv_r2, omega, nu_scale, cT, half_n, half_n_r2, inv_m;
     float w[Q], iw[Q];    // weights and their inverses (deviation storage)
     float wr[7], iwr[7];
+    // lattice sums of the float weights: sum_i w_i, sum_i |e_i|^2 w_i and
+    // sum_j (j-3)^2 wr_j (the deviation-space moment sums add these)
+    float sw0, sw2, swr2;
+    // Per-node reference storage (LBM_STORE_F16_NODE / BF16_NODE): records
+    // (rho - 1, rho t / 2, rho r u_x, rho r u_y), t = T - 1, after the
+    // populations of each buffer, and the per-population constants of the
+    // reference R_i - 1 = (rho - 1) + e_x (rho r u_x) + e_y (rho r u_y)
+    // + (|xi_i|^2 - D) rho t / 2 and R_j^h - 1 = t (ha_j + t hb_j) (ref_dev).
+    int nref;
+    const float4 *ref_src;
+    float4 *ref_dst;
+    static constexpr int NQ = (Q <= 49) ? Q : 1;
+    float pex[NQ], pey[NQ], kmD[NQ];
+    float ha[7], hb[7];
 };
+
+// t = T - 1 of a record, (rho t / 2) * 2 / rho with a correctly rounded
+// reciprocal: the same bits wherever it is evaluated.
+__device__ __forceinline__ float ref_t(float4 rc) { return (rc.y + rc.y) * __frcp_rn(1.0f + rc.x); }
+
+// Deviation of the reference R from 1 for population `pop` (translational
+// pop < Q, rotational pop - Q) under the record `rc`.  Writer and reader of a
+// stored value both call this with the same record floats; the fused
+// operations fix the rounding, so the reference cancels exactly.
+template <int Q, typename ST>
+__device__ __forceinline__ float ref_dev(const Params<Q, ST> &p, int pop, float4 rc, float ex, float ey,
+                                         float kmd)
+{
+    if (pop < Q) return fmaf(kmd, rc.y, fmaf(ey, rc.w, fmaf(ex, rc.z, rc.x)));
+    const int j = pop - Q;
+    const float t = ref_t(rc);
+    return t * fmaf(t, p.hb[j], p.ha[j]);
+}
+template <int Q, typename ST>
+__device__ __forceinline__ float ref_dev(const Params<Q, ST> &p, int pop, float4 rc)
+{
+    if constexpr (Q <= 49) {
+        if (pop < Q) return ref_dev(p, pop, rc, p.pex[pop], p.pey[pop], p.kmD[pop]);
+    }
+    return ref_dev(p, pop, rc, 0.f, 0.f, 0.f);
+}
 
 template <int Q, typename ST = float> Params<Q, ST> make_params(const Args &a)
 {
@@ -193,6 +235,42 @@ template <int Q, typename ST = float> Params<Q, ST> make_params(const Args &a)
     for (int j = 0; j < 7; ++j) {
         p.wr[j] = a.wr[j];
         p.iwr[j] = 1.0f / a.wr[j];
+    }
+    double s0 = 0.0, s2 = 0.0, sr2 = 0.0;
+    const D2Q37Table t37 = make_d2q37();
+    for (int i = 0; i < Q; ++i) {
+        // |e_i|^2 in each lattice's population order (the Lattice<> tables)
+        int e2 = 0;
+        if (Q == 37) e2 = t37.x[i] * t37.x[i] + t37.y[i] * t37.y[i];
+        else
+            for (int q = i, a3 = 0; a3 < 3 && (a3 == 0 || Q > (a3 == 1 ? 7 : 49)); ++a3, q /= 7)
+                e2 += (q % 7 - 3) * (q % 7 - 3);
+        s0 += (double)p.w[i];
+        s2 += (double)e2 * (double)p.w[i];
+    }
+    for (int j = 0; j < 7; ++j) sr2 += (double)((j - 3) * (j - 3)) * (double)p.wr[j];
+    p.sw0 = (float)s0;
+    p.sw2 = (float)s2;
+    p.swr2 = (float)sr2;
+    p.nref = a.storage >= 3;
+    p.ref_src = (p.nref && a.src)
+                    ? reinterpret_cast<const float4 *>(static_cast<const char *>(a.src) + a.ref_offset)
+                    : nullptr;
+    p.ref_dst = (p.nref && a.dst) ? reinterpret_cast<float4 *>(static_cast<char *>(a.dst) + a.ref_offset)
+                                  : nullptr;
+    const double rr = (double)a.r * (double)a.r;
+    for (int i = 0; i < Params<Q, ST>::NQ; ++i) {
+        int ex = 0, ey = 0;
+        if (Q == 37) { ex = t37.x[i]; ey = t37.y[i]; }
+        else if (Q <= 49) { ex = i % 7 - 3; ey = (Q == 49) ? i / 7 - 3 : 0; }
+        p.pex[i] = (float)ex;
+        p.pey[i] = (float)ey;
+        p.kmD[i] = (float)(rr * (ex * ex + ey * ey) - a.D);
+    }
+    for (int j = 0; j < 7; ++j) {
+        const double s2j = rr * (j - 3) * (j - 3);  // eta_j^2
+        p.ha[j] = (float)(0.5 * (s2j - 1.0));
+        p.hb[j] = (float)(0.125 * (s2j * s2j - 6.0 * s2j + 3.0));
     }
     return p;
 }
@@ -247,7 +325,22 @@ __device__ __forceinline__ float ld(const Params<Q, ST> &p, int pop, int off)
     else if constexpr (CG == 1) v = __ldcg(a);
     else v = __ldg(a);
     if constexpr (std::is_same<ST, float>::value) return v;
-    else return Storage<ST>::decode(v, pop < Q ? p.w[pop] : p.wr[pop - Q]);
+    else {
+        const float w = pop < Q ? p.w[pop] : p.wr[pop - Q];
+        float f = Storage<ST>::decode(v, w);
+        if (p.nref) f = fmaf(w, ref_dev(p, pop, p.ref_src[(uint32_t)off]), f);
+        return f;
+    }
+}
+// Store relative to the record `rc` (per-node reference storage).
+template <int Q, typename ST>
+__device__ __forceinline__ void st_ref(const Params<Q, ST> &p, int pop, int off, float v, float4 rc)
+{
+    if constexpr (!std::is_same<ST, float>::value) {
+        const float iw = pop < Q ? p.iw[pop] : p.iwr[pop - Q];
+        p.dst[(uint32_t)pop * (uint32_t)p.S + (uint32_t)off] =
+            Storage<ST>::from_dev(fmaf(v, iw, -1.0f) - ref_dev(p, pop, rc));
+    }
 }
 template <int Q, typename ST>
 __device__ __forceinline__ void st(const Params<Q, ST> &p, int pop, int off, float v)
@@ -670,6 +763,14 @@ __device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q, ST> &p, 
     using L = Lattice<LAT>;
     const int self = (z * p.Y + y) * p.pitch + x;
     const float *rho_in = p.in0, *u_in = p.in1, *T_in = p.in2;
+    float4 rc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (p.nref) {  // the node's reference: its own initial fields
+        const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
+        const float r0 = rho_in[node];
+        rc = make_float4(r0 - 1.0f, 0.5f * (r0 * (T_in[node] - 1.0f)), r0 * (p.r * u_in[node]),
+                         (L::D >= 2) ? r0 * (p.r * u_in[p.N + node]) : 0.f);
+        p.ref_dst[self] = rc;
+    }
 #pragma unroll 1
     for (int i = 0; i < L::Q; ++i) {
         const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
@@ -688,7 +789,8 @@ __device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q, ST> &p, 
         const EqCoef k = eq_coef<L::D>(T, ux * ux + uy * uy + uz * uz, rho);
         const float c = p.r * ((float)ex * ux + (float)ey * uy + (float)ez * uz);
         const float s = p.r2 * (float)(ex * ex + ey * ey + ez * ez);
-        st(p, i, self, p.w[i] * eq_single(k, c, s));
+        if (p.nref) st_ref(p, i, self, p.w[i] * eq_single(k, c, s), rc);
+        else st(p, i, self, p.w[i] * eq_single(k, c, s));
     }
     if (ROT) {
         const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
@@ -696,7 +798,10 @@ __device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q, ST> &p, 
         const float Tn = T_in[node];
         heq_node(p, Tn, Tn * p.inv_r2, heq);
 #pragma unroll
-        for (int j = 0; j < 7; ++j) st(p, L::Q + j, self, heq[j]);
+        for (int j = 0; j < 7; ++j) {
+            if (p.nref) st_ref(p, L::Q + j, self, heq[j], rc);
+            else st(p, L::Q + j, self, heq[j]);
+        }
     }
 }
 
@@ -835,10 +940,13 @@ __global__ void __launch_bounds__(kBlockX) k_set_state(const Params<Lattice<LAT>
     if (x >= p.X) return;
     const int self = (z * p.Y + y) * p.pitch + x;
     const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
+    if (p.nref) p.ref_dst[self] = make_float4(0.f, 0.f, 0.f, 0.f);  // rest reference: R = 1
     for (int i = 0; i < L::Q; ++i) st(p, i, self, p.in0[(int64_t)i * p.N + node]);
     if (ROT)
         for (int j = 0; j < 7; ++j) st(p, L::Q + j, self, p.in1[(int64_t)j * p.N + node]);
 }
+
+#include "lbm_step16.cuh"
 
 // ---------------------------------------------------------------------------
 // Host-side dispatch for one lattice.
@@ -856,6 +964,10 @@ cudaError_t launch_mode(Op op, const Args &a, cudaStream_t s)
     case Op::Step:
         if constexpr (LAT == 4) {  // 343 populations: the two-pass kernel
             return launch_step_q343<ROT, ST>(a, s);
+        } else if constexpr (MODE == 0 && !std::is_same<ST, float>::value) {
+            // 16-bit STREAM on the 1-D and 2-D lattices: deviation-space kernel
+            if (a.storage >= 3) k_step16<LAT, ROT, ST, true><<<grid, block, 0, s>>>(p);
+            else k_step16<LAT, ROT, ST, false><<<grid, block, 0, s>>>(p);
         } else {
             k_step<LAT, ROT, MODE><<<grid, block, 0, s>>>(p);
         }
@@ -889,8 +1001,8 @@ template <int LAT>
 cudaError_t launch_lattice(Op op, const Args &a, cudaStream_t s)
 {
     switch (a.storage) {
-    case 1: return launch_storage<LAT, __half>(op, a, s);
-    case 2: return launch_storage<LAT, __nv_bfloat16>(op, a, s);
+    case 1: case 3: return launch_storage<LAT, __half>(op, a, s);
+    case 2: case 4: return launch_storage<LAT, __nv_bfloat16>(op, a, s);
     default: return launch_storage<LAT, float>(op, a, s);
     }
 }

@@ -21,7 +21,7 @@ LATTICE_DIM = {"D1Q7": 1, "D2Q37": 2, "D2Q49": 2, "D3Q343": 3}
 LATTICE_Q = {"D1Q7": 7, "D2Q37": 37, "D2Q49": 49, "D3Q343": 343}
 BCS = {"periodic": 0, "copy": 1}
 MODES = {"stream": 0, "fd": 1}
-STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
+STORAGES = {"f32": 0, "f16": 1, "bf16": 2, "f16_node": 3, "bf16_node": 4}
 STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ESIZE", -3: "LBM_ECUDA",
           -4: "LBM_ENONFINITE", -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}
 

@@ -59,6 +59,10 @@ LBM_CASES = [  # lattice, n, shape, bc, mode, storage
     ("D2Q49", 2, (129, 3), ("copy", "copy"), "fd", "f16"),
     ("D3Q343", 2, (129, 3, 2), ("periodic", "copy", "periodic"), "stream", "f16"),
     ("D3Q343", 0, (33, 2, 3), ("periodic",) * 3, "stream", "f32"),
+    ("D2Q49", 3, (131, 5), ("periodic", "copy"), "stream", "bf16"),
+    ("D2Q49", 3, (130, 6), ("copy", "periodic"), "stream", "f16_node"),
+    ("D2Q37", 0, (67, 3), ("periodic", "periodic"), "stream", "bf16_node"),
+    ("D1Q7", 4, (259,), ("copy",), "stream", "bf16_node"),
 ]
 
 

@@ -35,6 +35,7 @@ def _current_state(sim):
     ("D2Q49", (100, 37), 3, "bf16"),
     ("D3Q343", (16, 16, 16), 0, "f16"),
     ("D3Q343", (12, 10, 9), 4, "bf16"),
+    ("D2Q49", (90, 33), 3, "bf16_node"),
     # 196,608 nodes want 768 reduction blocks: capped at 4 per SM
     ("D2Q49", (2048, 96), 3, "f16"),
 ])
