@@ -149,3 +149,43 @@ def test_full_size_blast_config_sampled(orc):
                + 1e-6 * np.abs(want).max())
         ratio = np.abs(got[k] - want) / tol
         assert np.all(ratio <= 1.0), (picks[k], ratio.max(), int(ratio.argmax()))
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("shape,bc,n", [((9, 7, 5), ("periodic",) * 3, 4),
+                                        ((40, 3, 4), ("copy", "periodic", "copy"), 0),
+                                        ((5, 6, 3), ("periodic", "copy", "periodic"), 2),
+                                        ((33, 2, 7), ("copy",) * 3, 4)])
+def test_one_step_per_population_16bit(orc, storage, shape, bc, n):
+    """Every stored population after one step of the 16-bit kernel (ragged
+    128-node tiles, rows narrower than the pull reach, the 6-plane
+    shared-memory stash) from a state the storage represents exactly, against the
+    oracle's FP64 step from the same state: within one unit in the last
+    place of the stored deviation plus float32 arithmetic (1e-5 of the
+    population's magnitude; 5e-5 for the seven populations that carry the
+    343-term correction sums)."""
+    from paper_1606_06107_gb300 import Lbm
+    wl = workloads.smooth_random(shape, seed=5, kind="D3Q343", n=n, bc=bc,
+                                 u_mean=(0.05, -0.03, 0.02))
+    g = Lbm("D3Q343", n, wl.tau, shape, bc, storage=storage)
+    ref = orc.Sim(orc.D3Q343, n, wl.tau, shape, tuple(0 if b == "periodic" else 1 for b in bc))
+    ref.set_macro(wl.rho, wl.u, wl.T)
+    ft, fr = ref.state()
+    g.set_state(ft.astype(np.float32), fr.astype(np.float32) if n else None)
+    ft0, fr0 = (x.cpu().numpy().astype(np.float64) for x in g.state())
+    ref.set_state(ft0, fr0 if n else None)
+    g.step(1)
+    ref.step(1)
+    assert g.status() == 0
+    gf, gr = (x.cpu().numpy().astype(np.float64) for x in g.state())
+    rf, rr = ref.state()
+    ulp = {"f16": 2.0 ** -10, "bf16": 2.0 ** -7}[storage]
+    _, _, w, _ = orc.lattice(orc.D3Q343)
+    wr = orc.heq(1.0)
+    corrected = {171, 170, 172, 164, 178, 122, 220}
+    for got, want, ws, extra in ((gf, rf, w, corrected), (gr, rr, wr, set())):
+        for i in range(got.shape[0]):
+            tol = 5e-5 if i in extra else 1e-5
+            bound = ws[i] * ulp * np.abs(want[i] / ws[i] - 1.0) + tol * np.abs(want[i]).max()
+            err = np.abs(got[i] - want[i])
+            assert np.all(err <= bound), (i, float((err - bound).max()))
