@@ -438,16 +438,23 @@ def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int =
     for s, _ in sims:
         s.close()
     q = lambda v, p: float(np.percentile(v, p)) if v.size else None
-    return {"metric": "surrogate speedup vs single-instance method at stated L1",
+    within = float((e_sur <= tol).sum() / max(1, e_all.size))
+    return {"metric": "surrogate speedup vs single-instance method at the measured rollout L1",
             "value": single_ms / sur_ms, "unit": "x",
             "config": f"{eval_tubes} held-out tubes x {L} nodes, K = {K} steps per call, "
                       f"{windows} calls ({windows * K} steps) from the initial state",
             "ms_per_call": sur_ms, "single_instance_ms_per_call": single_ms,
             "batched_method_ms_per_call": batched_ms,
             "ratio_vs_batched_method": batched_ms / sur_ms,
-            "stated_tol": tol,
+            # the checks bound each call (conservation residual and spot-check
+            # rel-L1 <= tol), not the error accumulated over the rollout: the
+            # speedup holds at the rollout accuracy reported beside it
+            "per_call_check_tol": tol,
+            "speedup_at": {"rollout_l1_p95": q(e_sur, 95), "rollout_l1_max": q(e_sur, 100),
+                           "fraction_of_scored_tubes_within_tol": within},
             "l1_vs_method_after_rollout": {"median": q(e_sur, 50), "p95": q(e_sur, 95),
                                            "max": q(e_sur, 100), "tubes": int(ok.sum()),
+                                           "within_tol": within,
                                            "non_finite_tubes": int((~finite).sum())},
             "network_alone": {"ms_per_call": net_ms,
                               "l1_median": q(e_net, 50), "l1_p95": q(e_net, 95),
@@ -458,7 +465,11 @@ def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int =
             "fallback_tubes": stats["fallback_tubes"],
             "method_failed_tubes": int(run.quarantined.sum()),
             "fallback_fraction": stats["fallback_tubes"] / ((windows + 1) * eval_tubes),
-            "max_spot_l1": stats["max_l1"],
+            # spot-check rel-L1 of the predictions before the decision (those
+            # above tol went to the method) and of the ones kept
+            "max_spot_l1_predicted": stats["max_l1"],
+            "max_spot_l1_accepted": stats["max_l1_accepted"],
+            "method_failed_tubes_excluded": int((~ok).sum()),
             "training": {"pairs": int(train_tubes * windows), "steps": total,
                          "batch_tubes": batch, "seconds": t_train, "cuda_graph": True,
                          "ms_per_step": t_train / total * 1e3, "loss_first": first,
@@ -788,7 +799,8 @@ def run_gpu(args):
             res = surrogate_leg(dev, train_tubes=args.surrogate_train_tubes,
                                 eval_tubes=args.surrogate_eval_tubes,
                                 windows=args.surrogate_windows,
-                                train_seconds=args.surrogate_seconds, patch=args.surrogate_patch)
+                                train_seconds=args.surrogate_seconds, patch=args.surrogate_patch,
+                                tol=args.surrogate_tol)
             add_peak(res["roofline"])
         elif args.only == "storage":
             res = storage_leg(dev, size=args.size, steps=args.storage_steps,
@@ -898,7 +910,7 @@ def run_gpu(args):
                                   eval_tubes=args.surrogate_eval_tubes,
                                   windows=args.surrogate_windows,
                                   train_seconds=args.surrogate_seconds,
-                                  patch=args.surrogate_patch)
+                                  patch=args.surrogate_patch, tol=args.surrogate_tol)
         add_peak(surrogate["roofline"])
     cpu = None
     if world == 1 and not args.no_cpu:
@@ -958,6 +970,8 @@ def main():
     ap.add_argument("--surrogate-windows", type=int, default=125)
     ap.add_argument("--surrogate-seconds", type=float, default=60.0)
     ap.add_argument("--surrogate-patch", type=int, default=4)
+    ap.add_argument("--surrogate-tol", type=float, default=1e-2,
+                    help="per-call tolerance of the surrogate's checks")
     ap.add_argument("--conv-impl", type=int, default=3,
                     help="convolution kernel for --only conv (include/lbm.h impl codes)")
     ap.add_argument("--batched-count", type=int, default=4096)

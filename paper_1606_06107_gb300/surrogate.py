@@ -575,6 +575,7 @@ class SurrogateRunner:
         self.l1 = torch.empty(B, dtype=torch.float32, device=dev)
         self._checks_h = torch.empty((2, B), dtype=torch.float32).pin_memory()
         self.stats = {"calls": 0, "fallback_tubes": 0, "max_residual": 0.0, "max_l1": 0.0,
+                      "max_l1_accepted": 0.0,
                       "method_failed": 0}
         self.quarantined = np.zeros(self.B, dtype=bool)
         self._solvers = {}
@@ -642,6 +643,9 @@ class SurrogateRunner:
         fin = np.isfinite(l1)
         if fin.any():
             self.stats["max_l1"] = max(self.stats["max_l1"], float(l1[fin].max()))
+        kept = ~bad & ~self.quarantined  # predictions that passed both checks
+        if kept.any():
+            self.stats["max_l1_accepted"] = max(self.stats["max_l1_accepted"], float(l1[kept].max()))
         return (r2, u2, T2), fallback
 
     def _fallback(self, rho, u, T, out, tubes):

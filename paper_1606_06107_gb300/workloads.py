@@ -61,6 +61,26 @@ def sod_1d(X: int = 1000, steps: int = 2000) -> Workload:
                     steps)
 
 
+def stream_tube(X: int = 1000, Y: int = 1, kind: str = "D1Q7", steps: int = 200,
+                rho_r: float = 0.25, p_r: float = 0.2) -> Workload:
+    """A Sod-type tube with Sod's temperature ratio 0.8: left rho=1, p=1,
+    u=0; right rho=rho_r, p=p_r, u=0.  The default (density ratio 4,
+    pressure ratio 5) is the strongest such tube the STREAM transport keeps
+    finite in double precision; rho_r=0.4, p_r=0.32 (ratios 2.5 and 3.1) the
+    strongest it keeps finite in float32 for 400 steps.  gamma = 1.4 with
+    n = 4 on D1Q7, or (kind "D2Q49", Y rows, periodic in y) gamma = 4/3 with
+    n = 4; tau = 2/3, copy ends in x.  200 steps reach t = 200/(X r) = 0.167."""
+    rho1, u1, T1 = _two_state_1d(X, (1.0, 0.0, 1.0), (rho_r, 0.0, p_r))
+    if kind == "D1Q7":
+        return Workload("stream_tube", kind, 4, 2.0 / 3.0, (X,), ("copy",), rho1, u1[None], T1,
+                        steps)
+    rho = np.tile(rho1, (Y, 1))
+    T = np.tile(T1, (Y, 1))
+    u = np.zeros((2, Y, X))
+    return Workload("stream_tube", kind, 4, 2.0 / 3.0, (X, Y), ("copy", "periodic"), rho, u, T,
+                    steps)
+
+
 def paper_tube_2d(X: int = 1000, Y: int = 16, kind: str = "D2Q37",
                   steps: int = 180) -> Workload:
     """The paper's own validation run (Sec. VI): 1000 x 16, left rho=4, T=1;
