@@ -2,8 +2,9 @@
 
 Workload: the four-quadrant 2-D Riemann problem on 2048 x 2048 nodes, D2Q49
 translational + D1Q7 rotational populations (gamma = 1.4, n = 3), tau = 2/3,
-periodic, float32, STREAM transport -- the stable-envelope variant of the
-seeded quadrant draws (see workloads.riemann_2d).  A step is one fused kernel
+periodic, float32, STREAM transport -- the widest stable-envelope variant of
+the seeded quadrant draws (rho in [0.8, 1.2], T in [0.6, 1.4], |u| <= 0.1:
+workloads.riemann_2d_wide; the stated draws go non-finite).  A step is one fused kernel
 launch over all nodes.  The state (2 x 940 MB) is larger than L2, so no flush
 is needed between steps.
 
@@ -123,7 +124,7 @@ def cpu_oracle_rate(seconds: float = 12.0, size: int = REF_SAMPLE, max_steps: in
     from oracle import oracle
     from paper_1606_06107_gb300 import workloads
 
-    wl = workloads.riemann_2d(size, size, seed=0, mild=True)
+    wl = workloads.riemann_2d_wide(size, size, seed=0)
     sim = oracle.Sim(oracle.D2Q49, wl.n, wl.tau, wl.shape, (oracle.PERIODIC,) * 2)
     sim.set_macro(wl.rho, wl.u, wl.T)
     sim.step(1)  # warm-up (page-in, thread pool)
@@ -166,10 +167,10 @@ def oracle_timing(budget: float = 8.0):
     sim = oracle.Sim(oracle.D1Q7, wl.n, wl.tau, wl.shape, (oracle.COPY,))
     sim.set_macro(wl.rho, wl.u, wl.T)
     out["sod_1d 1000 nodes, 2000 steps"] = timed([sim], 1000, 2000)
-    wl = workloads.riemann_2d(256, 256, seed=0, mild=True)
+    wl = workloads.riemann_2d_wide(256, 256, seed=0)
     sim = oracle.Sim(oracle.D2Q49, wl.n, wl.tau, wl.shape, (oracle.PERIODIC,) * 2)
     sim.set_macro(wl.rho, wl.u, wl.T)
-    out["riemann_2d_mild 256^2 D2Q49, up to 200 steps"] = timed([sim], 256 * 256, 200)
+    out["riemann_2d_wide 256^2 D2Q49, up to 200 steps"] = timed([sim], 256 * 256, 200)
     wl = workloads.blast_3d(L=64, radius=32 * 64 / 384, n=0, p_in=1.5, p_out=0.5)
     sim = oracle.Sim(oracle.D3Q343, 0, wl.tau, wl.shape, (oracle.PERIODIC,) * 3)
     sim.set_macro(wl.rho, wl.u, wl.T)
@@ -537,8 +538,8 @@ def conv_leg(dev, tubes: int = 1024, L: int = 4096, patch: int = 4, C: int = 128
     return out
 
 
-def blast_leg(dev, L: int = 384, steps: int = 10, storage: str = "f16", oracle_L: int = 32,
-              oracle_steps: int = 50):
+def blast_leg(dev, L: int = 384, steps: int = 10, storage: str = "f16", oracle_L: int = 64,
+              oracle_steps: int = 60, checkpoint: int = 20):
     """The 3-D blast workload on D3Q343: L^3 nodes, rho = 1, a central sphere
     of radius 32 L/384 at higher pressure, periodic, tau = 2/3, with the
     populations stored as `storage` deviations.  Stable-envelope variant
@@ -546,8 +547,10 @@ def blast_leg(dev, L: int = 384, steps: int = 10, storage: str = "f16", oracle_L
     puts T = 0.1 outside the 4th-order lattice's range and goes non-finite
     within ~10 steps.  For n = 0 (gamma = 5/3) and n = 4 (gamma = 9/7, the
     integer n nearest the stated gamma = 1.3).  Error against the FP64
-    oracle on the geometrically scaled oracle_L^3 problem after
-    oracle_steps steps."""
+    oracle on the geometrically scaled oracle_L^3 problem (sphere radius
+    32 oracle_L / 384: 5.33 nodes at 64^3, whose 2000 L / 384 = 333 steps
+    are the scaled run's length) at every `checkpoint` steps up to
+    oracle_steps, or to the first step the oracle's state is not finite."""
     import torch
 
     from oracle import oracle
@@ -575,24 +578,39 @@ def blast_leg(dev, L: int = 384, steps: int = 10, storage: str = "f16", oracle_L
         torch.cuda.empty_cache()
         Q = 343 + (7 if n else 0)
         gbs = L ** 3 * Q * 2 * 2 / (ms * 1e-3) / 1e9
-        # error against the FP64 oracle on the scaled problem
-        ws = workloads.blast_3d(L=oracle_L, radius=max(1.5, 32 * oracle_L / 384 * 2), n=n,
-                                p_in=1.5, p_out=0.5)
+        # error against the FP64 oracle on the scaled problem, at checkpoints
+        radius = 32 * oracle_L / 384 if oracle_L >= 64 else max(1.5, 64 * oracle_L / 384)
+        ws = workloads.blast_3d(L=oracle_L, radius=radius, n=n, p_in=1.5, p_out=0.5)
         s = Lbm("D3Q343", n, 2 / 3, ws.shape, ws.bc, device=dev, storage=storage)
         s.set_macro(ws.rho, ws.u, ws.T)
-        s.step(oracle_steps)
         ref = oracle.Sim(oracle.D3Q343, n, 2 / 3, ws.shape, (0, 0, 0))
         ref.set_macro(ws.rho, ws.u, ws.T)
-        ref.step(oracle_steps)
-        errs = [float(np.abs(x.cpu().numpy().astype(np.float64) - y).sum() / np.abs(y).sum())
-                for x, y in zip(s.moments(), ref.moments())]
+        checks, done, t_orc = [], 0, time.perf_counter()
+        while done < oracle_steps:
+            k = min(checkpoint, oracle_steps - done)
+            s.step(k)
+            ref.step(k)
+            done += k
+            want = ref.moments()
+            if not all(np.all(np.isfinite(y)) for y in want):
+                checks.append({"step": done, "oracle": "non-finite"})
+                break
+            errs = [float(np.abs(x.cpu().numpy().astype(np.float64) - y).sum() / np.abs(y).sum())
+                    for x, y in zip(s.moments(), want)]
+            checks.append({"step": done, "rho": errs[0], "u": errs[1], "T": errs[2]})
+        t_orc = time.perf_counter() - t_orc
+        last = [c for c in checks if "rho" in c][-1]
+        errs = [last["rho"], last["u"], last["T"]]
         out[f"n{n}"] = {"gamma": (3 + n + 2) / (3 + n), "ms_per_step": ms,
                         "value": L ** 3 / ms / 1e3, "unit": "Mnode-updates/s",
                         "algorithmic_GBps": gbs, "frac_of_hbm": gbs / hbm, "status": status,
                         "state_GB_two_buffers": state_gb,
                         "rel_l1_vs_fp64_oracle": {"rho": errs[0], "u": errs[1], "T": errs[2],
-                                                  "sample": f"{oracle_L}^3 scaled, "
-                                                            f"{oracle_steps} steps"}}
+                                                  "sample": f"{oracle_L}^3 scaled (sphere radius "
+                                                            f"{radius:.2f}), {last['step']} "
+                                                            f"steps",
+                                                  "checkpoints": checks,
+                                                  "oracle_seconds": t_orc}}
     out["workload"] = (f"blast_3d {L}^3 D3Q343, {storage} deviation storage, stable-envelope "
                        f"variant p 1.5 | 0.5")
     return out
@@ -601,7 +619,7 @@ def blast_leg(dev, L: int = 384, steps: int = 10, storage: str = "f16", oracle_L
 def storage_leg(dev, size: int = 2048, steps: int = 300,
                 storages=("f32", "f16", "bf16", "f16_node", "bf16_node"),
                 oracle_size: int = 256, oracle_steps: int = 100):
-    """The main 2-D workload (riemann_2d_mild, D2Q49 + D1Q7, STREAM) with each
+    """The main 2-D workload (riemann_2d_wide, D2Q49 + D1Q7, STREAM) with each
     population storage: time per fused step at size^2 (CUDA events around
     `steps` launches after 3 warm-up steps) and the algorithmic bandwidth at
     that storage's bytes per node-step; and the rel-L1 error in rho, u, T
@@ -613,8 +631,8 @@ def storage_leg(dev, size: int = 2048, steps: int = 300,
     from paper_1606_06107_gb300 import Lbm, workloads
 
     hbm, _ = peaks()
-    wl = workloads.riemann_2d(size, size, seed=0, mild=True)
-    ws = workloads.riemann_2d(oracle_size, oracle_size, seed=0, mild=True)
+    wl = workloads.riemann_2d_wide(size, size, seed=0)
+    ws = workloads.riemann_2d_wide(oracle_size, oracle_size, seed=0)
     ref = oracle.Sim(oracle.D2Q49, ws.n, ws.tau, ws.shape, (oracle.PERIODIC,) * 2)
     ref.set_macro(ws.rho, ws.u, ws.T)
     ref.step(oracle_steps)
@@ -751,7 +769,7 @@ def run_reference(args):
     rate, _, _, _ = cpu_oracle_rate(seconds=2.0, size=128)
     side = int(np.sqrt(rate * 1e6 * 90.0 / (args.steps + args.warmup)))
     side = max(32, min(REF_SAMPLE, side // 2 * 2))
-    wl = workloads.riemann_2d(side, side, seed=0, mild=True)
+    wl = workloads.riemann_2d_wide(side, side, seed=0)
     sim = oracle.Sim(oracle.D2Q49, wl.n, wl.tau, wl.shape, (oracle.PERIODIC,) * 2)
     sim.set_macro(wl.rho, wl.u, wl.T)
     sim.step(args.warmup)
@@ -807,7 +825,8 @@ def run_gpu(args):
                               storages=tuple(args.storages.split(",")))
         else:
             res = blast_leg(dev, L=args.blast_size, steps=args.blast_steps,
-                            oracle_L=min(16, args.blast_size), oracle_steps=5)
+                            oracle_L=min(args.blast_oracle_size, args.blast_size),
+                            oracle_steps=args.blast_oracle_steps)
             if args.blast_crop_steps > 0:
                 res["storage_error_crop"] = blast_storage_crop(dev, L=args.blast_size,
                                                                steps=args.blast_crop_steps,
@@ -824,7 +843,8 @@ def run_gpu(args):
             dist.barrier()
 
     X = Y = args.size
-    wl = workloads.riemann_2d(X, Y, seed=rank, mild=not args.stated)
+    wl = (workloads.riemann_2d(X, Y, seed=rank) if args.stated
+          else workloads.riemann_2d_wide(X, Y, seed=rank))
     stream = torch.cuda.current_stream()
     sim = Lbm(LATTICE, NROT, TAU, (X, Y), ("periodic", "periodic"), device=dev, stream=stream)
     rho = torch.tensor(wl.rho, dtype=torch.float32).pin_memory()
@@ -903,7 +923,8 @@ def run_gpu(args):
                               storages=tuple(args.storages.split(",")))
     blast = None
     if world == 1 and not args.no_blast:
-        blast = blast_leg(dev, L=args.blast_size, steps=args.blast_steps)
+        blast = blast_leg(dev, L=args.blast_size, steps=args.blast_steps,
+                          oracle_L=args.blast_oracle_size, oracle_steps=args.blast_oracle_steps)
     surrogate = None
     if world == 1 and not args.no_surrogate:
         surrogate = surrogate_leg(dev, train_tubes=args.surrogate_train_tubes,
@@ -978,6 +999,10 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=4000)
     ap.add_argument("--blast-size", type=int, default=384)
     ap.add_argument("--blast-steps", type=int, default=10)
+    ap.add_argument("--blast-oracle-size", type=int, default=64,
+                    help="edge of the scaled blast problem compared with the FP64 oracle")
+    ap.add_argument("--blast-oracle-steps", type=int, default=60,
+                    help="steps of that comparison (the scaled run's length is 333 at 64^3)")
     ap.add_argument("--blast-crop-steps", type=int, default=0,
                     help="with --only blast: also run the problem with f16 and with float "
                          "storage for this many steps and compare the central 64^3 crop")
