@@ -107,9 +107,10 @@ int lbm_set_mode(lbm_handle h, int mode, int m_fd);
  * (16 bytes per node, 14 % more bytes per step on D2Q49 + D1Q7):
  * (rho - 1, rho (T - 1) / 2, rho r u_x, rho r u_y) of the moments at which
  * the node last collided (set_macro: the initial fields; set_state: rest).  A
- * translational value is stored as s_i = f_i / w_i - R_i with the
- * first-order Hermite terms of the equilibrium of Sec. IV,
- * R_i = rho (1 + xi_i.u + (T - 1)(|xi_i|^2 - D) / 2), and a rotational value
+ * translational value is stored as s_i = f_i / w_i - R_i with the terms of
+ * the Hermite equilibrium of Sec. IV of first order in u and of up to second
+ * order in t = T - 1: R_i = rho (1 + xi_i.u + t (|xi_i|^2 - D) / 2)
+ * + (rho t)^2 (|xi_i|^4 - 2 (D+2) |xi_i|^2 + D (D+2)) / 8, and a rotational value
  * as s_j = h_j / w_j - h_j^eq(T) / w_j (its full equilibrium, which depends
  * on T only); a pulled value is decoded with the record of the node it was
  * pulled from.  Writer and reader evaluate R from the same stored floats

@@ -164,17 +164,22 @@ template <int Q, typename ST = float> struct Params {
     float wr[7], iwr[7];
     // lattice sums of the float weights: sum_i w_i, sum_i |e_i|^2 w_i and
     // sum_j (j-3)^2 wr_j (the deviation-space moment sums add these)
-    float sw0, sw2, swr2;
+    float sw0 = 0.f, sw2 = 0.f, swr2 = 0.f;
     // Per-node reference storage (LBM_STORE_F16_NODE / BF16_NODE): records
     // (rho - 1, rho t / 2, rho r u_x, rho r u_y), t = T - 1, after the
     // populations of each buffer, and the per-population constants of the
     // reference R_i - 1 = (rho - 1) + e_x (rho r u_x) + e_y (rho r u_y)
-    // + (|xi_i|^2 - D) rho t / 2 and R_j^h - 1 = t (ha_j + t hb_j) (ref_dev).
-    int nref;
-    const float4 *ref_src;
-    float4 *ref_dst;
+    // + (|xi_i|^2 - D) rho t / 2 + kt2_i (rho t / 2)^2, kt2_i = (|xi|^4 -
+    // 2 (D+2) |xi|^2 + D (D+2)) / 2 (the t^2 term of the Hermite
+    // equilibrium with rho^2 t^2 standing for rho t^2), and
+    // R_j^h - 1 = t (ha_j + t hb_j) (ref_dev).
+    // (Default off: kernels that fill a Params field by field, like the
+    // ensemble's, leave them so.)
+    int nref = 0;
+    const float4 *ref_src = nullptr;
+    float4 *ref_dst = nullptr;
     static constexpr int NQ = (Q <= 49) ? Q : 1;
-    float pex[NQ], pey[NQ], kmD[NQ];
+    float pex[NQ], pey[NQ], kmD[NQ], kt2[NQ];
     float ha[7], hb[7];
 };
 
@@ -188,9 +193,9 @@ __device__ __forceinline__ float ref_t(float4 rc) { return (rc.y + rc.y) * __frc
 // operations fix the rounding, so the reference cancels exactly.
 template <int Q, typename ST>
 __device__ __forceinline__ float ref_dev(const Params<Q, ST> &p, int pop, float4 rc, float ex, float ey,
-                                         float kmd)
+                                         float kmd, float kt2)
 {
-    if (pop < Q) return fmaf(kmd, rc.y, fmaf(ey, rc.w, fmaf(ex, rc.z, rc.x)));
+    if (pop < Q) return fmaf(kt2, rc.y * rc.y, fmaf(kmd, rc.y, fmaf(ey, rc.w, fmaf(ex, rc.z, rc.x))));
     const int j = pop - Q;
     const float t = ref_t(rc);
     return t * fmaf(t, p.hb[j], p.ha[j]);
@@ -199,9 +204,9 @@ template <int Q, typename ST>
 __device__ __forceinline__ float ref_dev(const Params<Q, ST> &p, int pop, float4 rc)
 {
     if constexpr (Q <= 49) {
-        if (pop < Q) return ref_dev(p, pop, rc, p.pex[pop], p.pey[pop], p.kmD[pop]);
+        if (pop < Q) return ref_dev(p, pop, rc, p.pex[pop], p.pey[pop], p.kmD[pop], p.kt2[pop]);
     }
-    return ref_dev(p, pop, rc, 0.f, 0.f, 0.f);
+    return ref_dev(p, pop, rc, 0.f, 0.f, 0.f, 0.f);
 }
 
 template <int Q, typename ST = float> Params<Q, ST> make_params(const Args &a)
@@ -265,7 +270,9 @@ template <int Q, typename ST = float> Params<Q, ST> make_params(const Args &a)
         else if (Q <= 49) { ex = i % 7 - 3; ey = (Q == 49) ? i / 7 - 3 : 0; }
         p.pex[i] = (float)ex;
         p.pey[i] = (float)ey;
-        p.kmD[i] = (float)(rr * (ex * ex + ey * ey) - a.D);
+        const double si = rr * (ex * ex + ey * ey);  // |xi_i|^2
+        p.kmD[i] = (float)(si - a.D);
+        p.kt2[i] = (float)(0.5 * (si * si - 2.0 * (a.D + 2) * si + a.D * (a.D + 2)));
     }
     for (int j = 0; j < 7; ++j) {
         const double s2j = rr * (j - 3) * (j - 3);  // eta_j^2
@@ -763,8 +770,9 @@ __device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q, ST> &p, 
     using L = Lattice<LAT>;
     const int self = (z * p.Y + y) * p.pitch + x;
     const float *rho_in = p.in0, *u_in = p.in1, *T_in = p.in2;
+    constexpr bool is16 = !std::is_same<ST, float>::value;
     float4 rc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (p.nref) {  // the node's reference: its own initial fields
+    if (is16 && p.nref) {  // the node's reference: its own initial fields
         const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
         const float r0 = rho_in[node];
         rc = make_float4(r0 - 1.0f, 0.5f * (r0 * (T_in[node] - 1.0f)), r0 * (p.r * u_in[node]),
@@ -789,7 +797,7 @@ __device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q, ST> &p, 
         const EqCoef k = eq_coef<L::D>(T, ux * ux + uy * uy + uz * uz, rho);
         const float c = p.r * ((float)ex * ux + (float)ey * uy + (float)ez * uz);
         const float s = p.r2 * (float)(ex * ex + ey * ey + ez * ez);
-        if (p.nref) st_ref(p, i, self, p.w[i] * eq_single(k, c, s), rc);
+        if (is16 && p.nref) st_ref(p, i, self, p.w[i] * eq_single(k, c, s), rc);
         else st(p, i, self, p.w[i] * eq_single(k, c, s));
     }
     if (ROT) {
@@ -799,7 +807,7 @@ __device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q, ST> &p, 
         heq_node(p, Tn, Tn * p.inv_r2, heq);
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
-            if (p.nref) st_ref(p, L::Q + j, self, heq[j], rc);
+            if (is16 && p.nref) st_ref(p, L::Q + j, self, heq[j], rc);
             else st(p, L::Q + j, self, heq[j]);
         }
     }
@@ -940,7 +948,8 @@ __global__ void __launch_bounds__(kBlockX) k_set_state(const Params<Lattice<LAT>
     if (x >= p.X) return;
     const int self = (z * p.Y + y) * p.pitch + x;
     const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
-    if (p.nref) p.ref_dst[self] = make_float4(0.f, 0.f, 0.f, 0.f);  // rest reference: R = 1
+    if constexpr (!std::is_same<ST, float>::value)
+        if (p.nref) p.ref_dst[self] = make_float4(0.f, 0.f, 0.f, 0.f);  // rest reference: R = 1
     for (int i = 0; i < L::Q; ++i) st(p, i, self, p.in0[(int64_t)i * p.N + node]);
     if (ROT)
         for (int j = 0; j < 7; ++j) st(p, L::Q + j, self, p.in1[(int64_t)j * p.N + node]);

@@ -82,7 +82,7 @@ k_step16(const Params<Lattice<LAT>::Q, ST> p)
         const int off = oy[3 - ey] + ox[3 - ex];
         d[I] = DV::get(__ldg(src + ((uint32_t)I * S + (uint32_t)off)));
         if constexpr (NREF)
-            d[I] += ref_dev(p, I, __ldg(p.ref_src + off), (float)ex, (float)ey, p.kmD[I]);
+            d[I] += ref_dev(p, I, __ldg(p.ref_src + off), (float)ex, (float)ey, p.kmD[I], p.kt2[I]);
     });
     float t_self = 0.f;
     if (ROT) {
@@ -143,7 +143,7 @@ k_step16(const Params<Lattice<LAT>::Q, ST> p)
         p.ref_dst[self] = rc;
     }
     auto put = [&](int pop, float ex, float ey, float kmd, float v) {
-        if constexpr (NREF) v -= ref_dev(p, pop, rc, ex, ey, kmd);
+        if constexpr (NREF) v -= ref_dev(p, pop, rc, ex, ey, kmd, p.kt2[pop]);
         out[(uint32_t)pop * S] = DV::put(v);
     };
     float acc0 = 0.f, acc2 = 0.f, accj[2] = {0.f, 0.f}, qm[2] = {0.f, 0.f}, qp[2] = {0.f, 0.f};
