@@ -36,7 +36,7 @@ BYTES_PER_NODE = (QT + QR) * 4 * 2          # every population read once, writte
 # workload, scaled by node count from a 1024^2 capture of the same kernel
 # (profiles/k_step_d2q49_stream_2048x2048.md); None whenever the kernel has
 # changed since that capture.
-NCU_TRAFFIC_BYTES = 1.6915e9
+NCU_TRAFFIC_BYTES = 1.6857e9
 REF_SAMPLE = 512                             # oracle sample grid for the CPU arms
 
 

@@ -143,6 +143,43 @@ template <> struct Storage<__nv_bfloat16> {
     __device__ static __nv_bfloat16 from_dev(float d) { return __float2bfloat16_rn(d); }
 };
 
+// Per-node reference storage (LBM_STORE_F16_NODE / BF16_NODE): the same
+// 2-byte values, as distinct types so that every kernel knows at compile
+// time whether a value is decoded with a reference record (ld, st_ref) and
+// the plain 16-bit kernels carry no reference code.
+struct NodeHalf {
+    __half v;
+};
+struct NodeBf16 {
+    __nv_bfloat16 v;
+};
+template <typename ST> struct NodeRef {
+    static constexpr bool value = false;
+    using elem = ST;
+};
+template <> struct NodeRef<NodeHalf> {
+    static constexpr bool value = true;
+    using elem = __half;
+};
+template <> struct NodeRef<NodeBf16> {
+    static constexpr bool value = true;
+    using elem = __nv_bfloat16;
+};
+template <typename N> struct NodeStorage {
+    using E = typename NodeRef<N>::elem;
+    __device__ static float decode(N v, float w) { return Storage<E>::decode(v.v, w); }
+    __device__ static N encode(float f, float inv_w) { return N{Storage<E>::encode(f, inv_w)}; }
+    __device__ static N from_dev(float d) { return N{Storage<E>::from_dev(d)}; }
+};
+template <> struct Storage<NodeHalf> : NodeStorage<NodeHalf> {};
+template <> struct Storage<NodeBf16> : NodeStorage<NodeBf16> {};
+using ::__ldcg;  // keep CUDA's overloads visible beside the two below
+using ::__ldg;
+__device__ __forceinline__ NodeHalf __ldg(const NodeHalf *a) { return NodeHalf{::__ldg(&a->v)}; }
+__device__ __forceinline__ NodeBf16 __ldg(const NodeBf16 *a) { return NodeBf16{::__ldg(&a->v)}; }
+__device__ __forceinline__ NodeHalf __ldcg(const NodeHalf *a) { return NodeHalf{::__ldcg(&a->v)}; }
+__device__ __forceinline__ NodeBf16 __ldcg(const NodeBf16 *a) { return NodeBf16{::__ldcg(&a->v)}; }
+
 // ---------------------------------------------------------------------------
 // Kernel parameters (passed by value: they live in the constant bank, so the
 // per-population weights become constant operands of the FMAs).
@@ -173,9 +210,8 @@ template <int Q, typename ST = float> struct Params {
     // 2 (D+2) |xi|^2 + D (D+2)) / 2 (the t^2 term of the Hermite
     // equilibrium with rho^2 t^2 standing for rho t^2), and
     // R_j^h - 1 = t (ha_j + t hb_j) (ref_dev).
-    // (Default off: kernels that fill a Params field by field, like the
-    // ensemble's, leave them so.)
-    int nref = 0;
+    // (Null unless the storage type is a NodeRef one; kernels that fill a
+    // Params field by field, like the ensemble's, leave them so.)
     const float4 *ref_src = nullptr;
     float4 *ref_dst = nullptr;
     static constexpr int NQ = (Q <= 49) ? Q : 1;
@@ -257,12 +293,12 @@ template <int Q, typename ST = float> Params<Q, ST> make_params(const Args &a)
     p.sw0 = (float)s0;
     p.sw2 = (float)s2;
     p.swr2 = (float)sr2;
-    p.nref = a.storage >= 3;
-    p.ref_src = (p.nref && a.src)
+    constexpr bool node = NodeRef<ST>::value;
+    p.ref_src = (node && a.src)
                     ? reinterpret_cast<const float4 *>(static_cast<const char *>(a.src) + a.ref_offset)
                     : nullptr;
-    p.ref_dst = (p.nref && a.dst) ? reinterpret_cast<float4 *>(static_cast<char *>(a.dst) + a.ref_offset)
-                                  : nullptr;
+    p.ref_dst = (node && a.dst) ? reinterpret_cast<float4 *>(static_cast<char *>(a.dst) + a.ref_offset)
+                                : nullptr;
     const double rr = (double)a.r * (double)a.r;
     for (int i = 0; i < Params<Q, ST>::NQ; ++i) {
         int ex = 0, ey = 0;
@@ -335,7 +371,7 @@ __device__ __forceinline__ float ld(const Params<Q, ST> &p, int pop, int off)
     else {
         const float w = pop < Q ? p.w[pop] : p.wr[pop - Q];
         float f = Storage<ST>::decode(v, w);
-        if (p.nref) f = fmaf(w, ref_dev(p, pop, p.ref_src[(uint32_t)off]), f);
+        if constexpr (NodeRef<ST>::value) f = fmaf(w, ref_dev(p, pop, p.ref_src[(uint32_t)off]), f);
         return f;
     }
 }
@@ -343,7 +379,7 @@ __device__ __forceinline__ float ld(const Params<Q, ST> &p, int pop, int off)
 template <int Q, typename ST>
 __device__ __forceinline__ void st_ref(const Params<Q, ST> &p, int pop, int off, float v, float4 rc)
 {
-    if constexpr (!std::is_same<ST, float>::value) {
+    if constexpr (NodeRef<ST>::value) {
         const float iw = pop < Q ? p.iw[pop] : p.iwr[pop - Q];
         p.dst[(uint32_t)pop * (uint32_t)p.S + (uint32_t)off] =
             Storage<ST>::from_dev(fmaf(v, iw, -1.0f) - ref_dev(p, pop, rc));
@@ -770,9 +806,9 @@ __device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q, ST> &p, 
     using L = Lattice<LAT>;
     const int self = (z * p.Y + y) * p.pitch + x;
     const float *rho_in = p.in0, *u_in = p.in1, *T_in = p.in2;
-    constexpr bool is16 = !std::is_same<ST, float>::value;
+    constexpr bool is_node = NodeRef<ST>::value;
     float4 rc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (is16 && p.nref) {  // the node's reference: its own initial fields
+    if constexpr (is_node) {  // the node's reference: its own initial fields
         const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
         const float r0 = rho_in[node];
         rc = make_float4(r0 - 1.0f, 0.5f * (r0 * (T_in[node] - 1.0f)), r0 * (p.r * u_in[node]),
@@ -797,7 +833,7 @@ __device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q, ST> &p, 
         const EqCoef k = eq_coef<L::D>(T, ux * ux + uy * uy + uz * uz, rho);
         const float c = p.r * ((float)ex * ux + (float)ey * uy + (float)ez * uz);
         const float s = p.r2 * (float)(ex * ex + ey * ey + ez * ez);
-        if (is16 && p.nref) st_ref(p, i, self, p.w[i] * eq_single(k, c, s), rc);
+        if constexpr (is_node) st_ref(p, i, self, p.w[i] * eq_single(k, c, s), rc);
         else st(p, i, self, p.w[i] * eq_single(k, c, s));
     }
     if (ROT) {
@@ -807,7 +843,7 @@ __device__ __forceinline__ void init_node(const Params<Lattice<LAT>::Q, ST> &p, 
         heq_node(p, Tn, Tn * p.inv_r2, heq);
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
-            if (is16 && p.nref) st_ref(p, L::Q + j, self, heq[j], rc);
+            if constexpr (is_node) st_ref(p, L::Q + j, self, heq[j], rc);
             else st(p, L::Q + j, self, heq[j]);
         }
     }
@@ -948,14 +984,14 @@ __global__ void __launch_bounds__(kBlockX) k_set_state(const Params<Lattice<LAT>
     if (x >= p.X) return;
     const int self = (z * p.Y + y) * p.pitch + x;
     const int64_t node = ((int64_t)z * p.Y + y) * p.X + x;
-    if constexpr (!std::is_same<ST, float>::value)
-        if (p.nref) p.ref_dst[self] = make_float4(0.f, 0.f, 0.f, 0.f);  // rest reference: R = 1
+    if constexpr (NodeRef<ST>::value)
+        p.ref_dst[self] = make_float4(0.f, 0.f, 0.f, 0.f);  // rest reference: R = 1
     for (int i = 0; i < L::Q; ++i) st(p, i, self, p.in0[(int64_t)i * p.N + node]);
     if (ROT)
         for (int j = 0; j < 7; ++j) st(p, L::Q + j, self, p.in1[(int64_t)j * p.N + node]);
 }
 
-#include "lbm_step16.cuh"
+#include "lbm_step_node.cuh"
 
 // ---------------------------------------------------------------------------
 // Host-side dispatch for one lattice.
@@ -973,10 +1009,9 @@ cudaError_t launch_mode(Op op, const Args &a, cudaStream_t s)
     case Op::Step:
         if constexpr (LAT == 4) {  // 343 populations: the two-pass kernel
             return launch_step_q343<ROT, ST>(a, s);
-        } else if constexpr (MODE == 0 && !std::is_same<ST, float>::value) {
-            // 16-bit STREAM on the 1-D and 2-D lattices: deviation-space kernel
-            if (a.storage >= 3) k_step16<LAT, ROT, ST, true><<<grid, block, 0, s>>>(p);
-            else k_step16<LAT, ROT, ST, false><<<grid, block, 0, s>>>(p);
+        } else if constexpr (NodeRef<ST>::value) {
+            // per-node references: the deviation-space kernel (STREAM only)
+            k_step_node<LAT, ROT, ST><<<grid, block, 0, s>>>(p);
         } else {
             k_step<LAT, ROT, MODE><<<grid, block, 0, s>>>(p);
         }
@@ -999,6 +1034,13 @@ template <int LAT, typename ST>
 cudaError_t launch_storage(Op op, const Args &a, cudaStream_t s)
 {
     const bool rot = a.Qr > 0;
+    if constexpr (NodeRef<ST>::value) {  // STREAM on the 1-D and 2-D lattices only (host checks)
+        if constexpr (LAT == 4) return cudaErrorInvalidValue;
+        else {
+            if (a.mode != 0) return cudaErrorInvalidValue;
+            return rot ? launch_mode<LAT, true, 0, ST>(op, a, s) : launch_mode<LAT, false, 0, ST>(op, a, s);
+        }
+    }
     if (a.mode == 0 || LAT == 4)  // D3Q343 has no FD transport (the host rejects it)
         return rot ? launch_mode<LAT, true, 0, ST>(op, a, s) : launch_mode<LAT, false, 0, ST>(op, a, s);
     if constexpr (LAT != 4)
@@ -1010,8 +1052,10 @@ template <int LAT>
 cudaError_t launch_lattice(Op op, const Args &a, cudaStream_t s)
 {
     switch (a.storage) {
-    case 1: case 3: return launch_storage<LAT, __half>(op, a, s);
-    case 2: case 4: return launch_storage<LAT, __nv_bfloat16>(op, a, s);
+    case 1: return launch_storage<LAT, __half>(op, a, s);
+    case 2: return launch_storage<LAT, __nv_bfloat16>(op, a, s);
+    case 3: return launch_storage<LAT, NodeHalf>(op, a, s);
+    case 4: return launch_storage<LAT, NodeBf16>(op, a, s);
     default: return launch_storage<LAT, float>(op, a, s);
     }
 }

@@ -1,42 +1,40 @@
-// The STREAM step for 16-bit population storage (LBM_STORE_F16 /
-// LBM_STORE_BF16) on the 1-D and 2-D lattices.  Included by lbm_step.cuh
-// inside namespace lbm; uses its lattices, parameters, equilibria and
-// moments.
+// The STREAM step for per-node reference storage (LBM_STORE_F16_NODE /
+// LBM_STORE_BF16_NODE) on the 1-D and 2-D lattices.  Included by
+// lbm_step.cuh inside namespace lbm; uses its lattices, parameters,
+// equilibria, moments and reference records (ref_dev).
 //
-// Stored format: the relative deviation from the rest equilibrium,
-// d_i = f_i / w_i - 1, in IEEE half or bfloat16 (what k_init, k_get_state
-// and the other kernels of lbm_step.cuh read and write).  All arithmetic is
-// float32, except the temperature's kinetic-energy subtraction, which is
-// double (make_moments).
+// Stored format: a translational value is s_i = f_i / w_i - R_i with R_i the
+// node's reference (Params: first order in u, up to second order in T - 1 of
+// the Hermite equilibrium), a rotational value s_j = h_j / w_j - h_j^eq(T) / w_j,
+// in IEEE half or bfloat16; each node's record (rho - 1, rho t / 2, rho r u_x,
+// rho r u_y) follows the populations.  All arithmetic is float32, except the
+// temperature's kinetic-energy subtraction, which is double (make_moments).
 //
-// Against the float kernel k_step this kernel changes two things, each to
-// cut instructions per node (the 16-bit step is bound by issue and latency,
-// not by its bytes):
-//  - It computes on the deviations themselves.  With v = f / w = 1 + d,
-//    the post-collision deviation is d* = (1 - omega) d + omega rho P - omega,
-//    where P = g^eq / (w rho), so a value needs no multiply-add to decode
-//    or to encode.  The moment sums are sum_i w_i d_i plus the constant
-//    lattice sums of the float weights.
-//  - The rotational update works on deviations too: the upwind stencil of a
-//    constant is zero, so advecting d is advecting h / w.
-// With NREF (LBM_STORE_F16_NODE / BF16_NODE) a stored value is the
-// deviation from the reference of its node instead of from rest: the pull
-// adds the reference deviation ref_dev() of the source node's record, the
-// collision is unchanged, and the store subtracts that of the node's new
-// record, (rho - 1, rho t / 2, rho r u_x, rho r u_y) of the moments just
-// taken, which it also writes.  The rotational stencil decodes each value
-// with the record of the node it is read from.
+// The kernel computes on the deviations from rest d = f / w - 1: the pull
+// adds the reference deviation ref_dev() of the source node's record to the
+// stored value, the post-collision deviation is
+// d* = (1 - omega) d + omega rho P - omega (P = g^eq / (w rho)), so a value
+// needs no multiply-add to decode or encode, and the moment sums are
+// sum_i w_i d_i plus the constant lattice sums of the float weights.  The
+// store subtracts the reference deviation of the node's new record, the
+// moments just taken, which it also writes.  The rotational update works on
+// deviations too (the upwind stencil of a constant is zero); each value of
+// its stencil is decoded with the record of the node it is read from.
 //
-// Measured and dropped: two x-adjacent nodes per thread with packed 32-bit
-// loads and stores took 17 % fewer instructions per node but 168 registers,
-// so it held 11 resident warps per SM instead of 19 and ran 30 % slower;
-// one pointer per source column with block-uniform row offsets issued 5 %
-// more instructions than integer offsets.
+// Measured and dropped: the same deviation-space form for rest storage
+// (68.3 warp instructions per node against 63.6 for k_step with 16-bit
+// values, 2 % slower); two x-adjacent nodes per thread with packed 32-bit
+// loads and stores (17 % fewer instructions per node but 168 registers, so
+// 11 resident warps per SM instead of 19, 30 % slower); one pointer per
+// source column with block-uniform row offsets (5 % more instructions than
+// integer offsets).
 #pragma once
 
-// Resident 128-thread blocks per SM the register allocation must allow.
-#ifndef LBM_STEP16_MIN_BLOCKS
-#define LBM_STEP16_MIN_BLOCKS 5
+// Resident 128-thread blocks per SM the register allocation must allow
+// (A/B on the 2048^2 workload: 3 / 4 / 5 / 6 blocks gave 6,969 / 8,089 /
+// 8,187 / 7,870 Mnode/s with bfloat16 node references).
+#ifndef LBM_STEP_NODE_MIN_BLOCKS
+#define LBM_STEP_NODE_MIN_BLOCKS 5
 #endif
 
 template <typename ST> struct Dev16;
@@ -49,12 +47,12 @@ template <> struct Dev16<__nv_bfloat16> {
     __device__ static unsigned short put(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
 };
 
-template <int LAT, bool ROT, typename ST, bool NREF>
-__global__ void __launch_bounds__(kBlockX, LBM_STEP16_MIN_BLOCKS)
-k_step16(const Params<Lattice<LAT>::Q, ST> p)
+template <int LAT, bool ROT, typename ST>
+__global__ void __launch_bounds__(kBlockX, LBM_STEP_NODE_MIN_BLOCKS)
+k_step_node(const Params<Lattice<LAT>::Q, ST> p)
 {
     using L = Lattice<LAT>;
-    using DV = Dev16<ST>;
+    using DV = Dev16<typename NodeRef<ST>::elem>;
     constexpr int Q = L::Q;
     constexpr int D = L::D;
     constexpr int C = (Q - 1) / 2;
@@ -81,16 +79,15 @@ k_step16(const Params<Lattice<LAT>::Q, ST> p)
         constexpr int ex = L::ex(I), ey = L::ey(I);
         const int off = oy[3 - ey] + ox[3 - ex];
         d[I] = DV::get(__ldg(src + ((uint32_t)I * S + (uint32_t)off)));
-        if constexpr (NREF)
-            d[I] += ref_dev(p, I, __ldg(p.ref_src + off), (float)ex, (float)ey, p.kmD[I], p.kt2[I]);
+        d[I] += ref_dev(p, I, __ldg(p.ref_src + off), (float)ex, (float)ey, p.kmD[I], p.kt2[I]);
     });
     float t_self = 0.f;
     if (ROT) {
-        if constexpr (NREF) t_self = ref_t(__ldg(p.ref_src + self));
+        t_self = ref_t(__ldg(p.ref_src + self));
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
             h[j] = DV::get(__ldg(src + ((uint32_t)(Q + j) * S + (uint32_t)self)));
-            if constexpr (NREF) h[j] += t_self * fmaf(t_self, p.hb[j], p.ha[j]);
+            h[j] += t_self * fmaf(t_self, p.hb[j], p.ha[j]);
         }
     }
 
@@ -137,13 +134,10 @@ k_step16(const Params<Lattice<LAT>::Q, ST> p)
     const EqCoef k = eq_coef<D>(m.T, m.ux * m.ux + m.uy * m.uy, p.omega * m.rho);  // omega rho P
     const float ru[2] = {m.ux * p.r, m.uy * p.r};
     // this node's new reference record (what the next step's readers decode with)
-    float4 rc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if constexpr (NREF) {
-        rc = make_float4(m.rho - 1.0f, 0.5f * (m.rho * (m.T - 1.0f)), m.rho * ru[0], m.rho * ru[1]);
-        p.ref_dst[self] = rc;
-    }
+    const float4 rc = make_float4(m.rho - 1.0f, 0.5f * (m.rho * (m.T - 1.0f)), m.rho * ru[0], m.rho * ru[1]);
+    p.ref_dst[self] = rc;
     auto put = [&](int pop, float ex, float ey, float kmd, float v) {
-        if constexpr (NREF) v -= ref_dev(p, pop, rc, ex, ey, kmd, p.kt2[pop]);
+        v -= ref_dev(p, pop, rc, ex, ey, kmd, p.kt2[pop]);
         out[(uint32_t)pop * S] = DV::put(v);
     };
     float acc0 = 0.f, acc2 = 0.f, accj[2] = {0.f, 0.f}, qm[2] = {0.f, 0.f}, qp[2] = {0.f, 0.f};
@@ -194,12 +188,12 @@ k_step16(const Params<Lattice<LAT>::Q, ST> p)
     // ---- rotational populations: upwind advection of the deviations -------
     if (ROT) {
         float heq[7], adv[7], adv_t1 = 0.f, adv_t2 = 0.f;
-        const float t_new = NREF ? ref_t(rc) : 0.f;
+        const float t_new = ref_t(rc);
         heq_node(p, m.T, m.T_lat, heq);
 #pragma unroll
         for (int j = 0; j < 7; ++j) adv[j] = 0.f;
         // One axis: the values two and one nodes upwind and one downwind.
-        // With NREF each neighbour value adds t (ha_j + t hb_j) of its own
+        // Each neighbour value adds t (ha_j + t hb_j) of its own
         // node, so their references enter as ha_j T1 + hb_j T2, with T1, T2
         // the stencil applied to t and t^2 of the three neighbours (this
         // node's own value h[j] is decoded already, its stencil slot is 0).
@@ -212,12 +206,10 @@ k_step16(const Params<Lattice<LAT>::Q, ST> p)
                                      DV::get(__ldg(src + (o + (uint32_t)u1))), h[j],
                                      DV::get(__ldg(src + (o + (uint32_t)d1))));
             }
-            if constexpr (NREF) {
-                const float tuu = ref_t(__ldg(p.ref_src + uu)), tu1 = ref_t(__ldg(p.ref_src + u1));
-                const float td1 = ref_t(__ldg(p.ref_src + d1));
-                adv_t1 += upwind_abs(anu, tuu, tu1, 0.f, td1);
-                adv_t2 += upwind_abs(anu, tuu * tuu, tu1 * tu1, 0.f, td1 * td1);
-            }
+            const float tuu = ref_t(__ldg(p.ref_src + uu)), tu1 = ref_t(__ldg(p.ref_src + u1));
+            const float td1 = ref_t(__ldg(p.ref_src + d1));
+            adv_t1 += upwind_abs(anu, tuu, tu1, 0.f, td1);
+            adv_t2 += upwind_abs(anu, tuu * tuu, tu1 * tu1, 0.f, td1 * td1);
         };
         {
             const float nu = m.ux * p.nu_scale;
@@ -233,9 +225,9 @@ k_step16(const Params<Lattice<LAT>::Q, ST> p)
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
             float a = adv[j];
-            if constexpr (NREF) a = fmaf(p.ha[j], adv_t1, fmaf(p.hb[j], adv_t2, a));
+            a = fmaf(p.ha[j], adv_t1, fmaf(p.hb[j], adv_t2, a));
             float v = fmaf(keep, h[j], fmaf(om, heq[j] * p.iwr[j], -om) - a);
-            if constexpr (NREF) v -= t_new * fmaf(t_new, p.hb[j], p.ha[j]);
+            v -= t_new * fmaf(t_new, p.hb[j], p.ha[j]);
             out[(uint32_t)(Q + j) * S] = DV::put(v);
         }
     }

@@ -98,9 +98,10 @@ def test_one_step_per_population_16bit(orc, storage, kind, shape, bc, n):
     the same state: within one unit in the last place of the stored
     deviation (half an ulp of rounding plus float32 arithmetic that may
     cross a rounding boundary) plus the float32 allowance of the other
-    one-step tests, 1e-5 of the population's magnitude.  Ragged widths, odd
-    widths (a thread's second node past the row), grids narrower than the
-    pull reach, wrap and clamp at both ends."""
+    one-step tests, 1e-5 of the population's magnitude.  Ragged and odd
+    widths (partial 128-node tiles), grids narrower than the pull reach, wrap
+    and clamp at both ends; with the per-node reference storages, states
+    whose records were written by set_state (rest) and by the step."""
     from paper_1606_06107_gb300 import Lbm
     D = len(shape)
     wl = workloads.smooth_random(shape, seed=4, kind=kind, n=n, bc=bc,
