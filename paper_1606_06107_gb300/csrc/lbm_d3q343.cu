@@ -44,10 +44,20 @@ constexpr int kQ343 = 343;
 #ifndef LBM_Q343_STASH_FLOAT
 #define LBM_Q343_STASH_FLOAT 0
 #endif
+// Threads per block of the step (x positions of one row).  Measured on the
+// 384^3 f16 blast (ms per step, n = 0 / n = 4): 128 threads at 3 blocks per
+// SM 34.1 / 39.8; 64 at 6 36.6 / 42.4; 64 at 7 with 5 stash planes 49.6 /
+// 55.7; 64 at 8 with 4 planes 42.7 / 49.8; 32 at 12 47.5 / 55.0.  Narrower
+// blocks share fewer of the pulled rows' lines in L1.
+#ifndef LBM_Q343_BLOCK
+#define LBM_Q343_BLOCK 128
+#endif
+constexpr int kQ343Block = LBM_Q343_BLOCK;
+
 template <typename ST> struct StashPlanes {
     static constexpr int value = std::is_same<ST, float>::value ? LBM_Q343_STASH_FLOAT : LBM_Q343_STASH_HALF;
 };
-template <typename ST> constexpr size_t stash_bytes() { return (size_t)StashPlanes<ST>::value * 49 * kBlockX * sizeof(ST); }
+template <typename ST> constexpr size_t stash_bytes() { return (size_t)StashPlanes<ST>::value * 49 * kQ343Block * sizeof(ST); }
 
 template <int Q, typename ST>
 __device__ __forceinline__ float decode_pop(const Params<Q, ST> &p, int pop, ST v)
@@ -57,11 +67,11 @@ __device__ __forceinline__ float decode_pop(const Params<Q, ST> &p, int pop, ST 
 }
 
 template <bool ROT, typename ST>
-__global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(const Params<kQ343, ST> p)
+__global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(const Params<kQ343, ST> p)
 {
     constexpr int D = 3;
     constexpr int C = (kQ343 - 1) / 2;  // rest velocity (171)
-    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    const int x = blockIdx.x * kQ343Block + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= p.X) return;
     const Offsets o = node_offsets<D>(p, x, y, z);
@@ -73,7 +83,7 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
     for (int a = 0; a < 7; ++a) cs[a] = 0.f;
     float rho = 0.f, jy = 0.f, jz = 0.f, e2yz = 0.f;
     extern __shared__ unsigned char q343_smem[];
-    ST *stash = reinterpret_cast<ST *>(q343_smem);  // [NS planes x 49][kBlockX] raw values
+    ST *stash = reinterpret_cast<ST *>(q343_smem);  // [NS planes x 49][kQ343Block] raw values
     constexpr int NS = StashPlanes<ST>::value;
     // e_y is unrolled so that each e_z plane issues its 49 loads at once
     auto plane1 = [&](auto keep, int c) {
@@ -87,7 +97,7 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
             for (int a = 0; a < 7; ++a) {
                 const int i = (c * 7 + b) * 7 + a;
                 const ST v = __ldg(p.src + ((uint64_t)i * (uint64_t)p.S + (uint64_t)(uint32_t)(row + o.x[6 - a])));
-                if constexpr (KEEP) stash[i * kBlockX + threadIdx.x] = v;
+                if constexpr (KEEP) stash[i * kQ343Block + threadIdx.x] = v;
                 const float g = decode_pop(p, i, v);
                 cs[a] += g;
                 rsum += g;
@@ -155,7 +165,7 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
                 r2 = fmaf((float)E2, q, r2);
                 if (ex) rx = fmaf((float)ex, q, rx);
                 float g;
-                if constexpr (KEPT) g = decode_pop(p, i, stash[i * kBlockX + threadIdx.x]);
+                if constexpr (KEPT) g = decode_pop(p, i, stash[i * kQ343Block + threadIdx.x]);
                 else g = ld(p, i, row + o.x[6 - a]);
                 if (E2 <= 1) {  // the rest and the six unit velocities: stored last
                     if (E2 == 0) { q_c = q; g_c = g; }
@@ -210,7 +220,7 @@ __global__ void __launch_bounds__(kBlockX, LBM_Q343_MIN_BLOCKS) k_step_q343(cons
 template <bool ROT, typename ST> cudaError_t launch_step_q343(const Args &a, cudaStream_t s)
 {
     const auto p = make_params<kQ343, ST>(a);
-    const dim3 grid((a.X + kBlockX - 1) / kBlockX, a.Y, a.Z);
+    const dim3 grid((a.X + kQ343Block - 1) / kQ343Block, a.Y, a.Z);
     constexpr size_t sh = stash_bytes<ST>();
     if constexpr (sh > 48 * 1024) {  // the opt-in limit is a per-device function attribute
         static std::atomic<bool> done[64];
@@ -225,7 +235,7 @@ template <bool ROT, typename ST> cudaError_t launch_step_q343(const Args &a, cud
             done[dev].store(true);
         }
     }
-    k_step_q343<ROT, ST><<<grid, kBlockX, sh, s>>>(p);
+    k_step_q343<ROT, ST><<<grid, kQ343Block, sh, s>>>(p);
     return cudaGetLastError();
 }
 
