@@ -1035,17 +1035,19 @@ cudaError_t launch_storage(Op op, const Args &a, cudaStream_t s)
 {
     const bool rot = a.Qr > 0;
     if constexpr (NodeRef<ST>::value) {  // STREAM on the 1-D and 2-D lattices only (host checks)
-        if constexpr (LAT == 4) return cudaErrorInvalidValue;
-        else {
+        if constexpr (LAT == 4) {
+            return cudaErrorInvalidValue;
+        } else {
             if (a.mode != 0) return cudaErrorInvalidValue;
             return rot ? launch_mode<LAT, true, 0, ST>(op, a, s) : launch_mode<LAT, false, 0, ST>(op, a, s);
         }
+    } else {
+        if (a.mode == 0 || LAT == 4)  // D3Q343 has no FD transport (the host rejects it)
+            return rot ? launch_mode<LAT, true, 0, ST>(op, a, s) : launch_mode<LAT, false, 0, ST>(op, a, s);
+        if constexpr (LAT != 4)
+            return rot ? launch_mode<LAT, true, 1, ST>(op, a, s) : launch_mode<LAT, false, 1, ST>(op, a, s);
+        return cudaErrorInvalidValue;
     }
-    if (a.mode == 0 || LAT == 4)  // D3Q343 has no FD transport (the host rejects it)
-        return rot ? launch_mode<LAT, true, 0, ST>(op, a, s) : launch_mode<LAT, false, 0, ST>(op, a, s);
-    if constexpr (LAT != 4)
-        return rot ? launch_mode<LAT, true, 1, ST>(op, a, s) : launch_mode<LAT, false, 1, ST>(op, a, s);
-    return cudaErrorInvalidValue;
 }
 
 template <int LAT>
