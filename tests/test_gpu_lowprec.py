@@ -174,3 +174,51 @@ def test_node_reference_is_more_accurate(orc, prec):
     gain = {"f16": 3.0, "bf16": 5.0}[prec]
     assert node[1] * gain <= rest[1], errs
     assert node[0] <= rest[0] and node[2] <= rest[2], errs
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16_node"])
+def test_full_size_bench_config_sampled_16bit(orc, storage):
+    """The storage leg's configuration at full size (2048 x 2048 D2Q49 + D1Q7,
+    the four-quadrant workload, periodic): after 20 GPU steps, one more GPU
+    step against one oracle step from the same decoded state, every
+    population within the one-step 16-bit bound above."""
+    import torch
+    from paper_1606_06107_gb300 import Lbm
+    wl = workloads.riemann_2d_wide(2048, 2048, seed=0)
+    gpu = Lbm(wl.kind, wl.n, wl.tau, wl.shape, wl.bc, storage=storage)
+    gpu.set_macro(wl.rho, wl.u, wl.T)
+    gpu.step(20)
+    ref = orc.Sim(orc.D2Q49, wl.n, wl.tau, wl.shape, (0, 0))
+    ft, fr = (x.cpu().numpy().astype(np.float64) for x in gpu.state())
+    ref.set_state(ft, fr)
+    del ft, fr
+    rho, u, T = ref.moments()
+    gpu.step(1)
+    ref.step(1)
+    torch.cuda.synchronize()
+    assert gpu.status() == 0
+    ulp = {"f16": 2.0 ** -10, "bf16": 2.0 ** -7}[storage.split("_")[0]]
+    r, e, w, _ = orc.lattice(orc.D2Q49)
+    wr = orc.heq(1.0)
+    got_t, got_r = gpu.state()
+    want_t, want_r = ref.state()
+    t = T - 1.0
+    eta2 = (r * (np.arange(7) - 3.0)) ** 2
+    for i in range(49):
+        xi = r * e[i, :2].astype(float)
+        s2 = float((xi ** 2).sum())
+        Rm1 = 0.0
+        if storage.endswith("_node"):
+            Rm1 = (rho * (1 + xi[0] * u[0] + xi[1] * u[1] + 0.5 * t * (s2 - 2)) - 1.0
+                   + (rho * t) ** 2 * (s2 ** 2 - 8 * s2 + 8) / 8)
+        want = want_t[i]
+        bound = w[i] * ulp * (np.abs(want / w[i] - 1.0) + np.abs(Rm1)) + 1e-5 * np.abs(want).max()
+        err = np.abs(got_t[i].cpu().numpy().astype(np.float64) - want)
+        assert np.all(err <= bound), (i, float((err - bound).max()))
+    for j in range(7):
+        Rm1 = t * (0.5 * (eta2[j] - 1) + 0.125 * t * (eta2[j] ** 2 - 6 * eta2[j] + 3)) \
+            if storage.endswith("_node") else 0.0
+        want = want_r[j]
+        bound = wr[j] * ulp * (np.abs(want / wr[j] - 1.0) + np.abs(Rm1)) + 1e-5 * np.abs(want).max()
+        err = np.abs(got_r[j].cpu().numpy().astype(np.float64) - want)
+        assert np.all(err <= bound), ("h", j, float((err - bound).max()))

@@ -312,7 +312,7 @@ def test_full_size_bench_config_sampled(orc):
     GPU step is compared with one oracle step from the same float32 state,
     population by population; mass and momentum stay conserved."""
     import torch
-    wl = workloads.riemann_2d(2048, 2048, seed=0, mild=True)
+    wl = workloads.riemann_2d_wide(2048, 2048, seed=0)
     gpu, ref = make_pair(orc, wl)
     gpu.set_macro(wl.rho, wl.u, wl.T)
     c0 = gpu.conservation()
