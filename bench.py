@@ -277,7 +277,8 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
 
 def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int = 4096,
                   K: int = 32, windows: int = 125, train_seconds: float = 60.0, patch: int = 4,
-                  batch: int = 32, single_sample: int = 16, tol: float = 1e-2):
+                  batch: int = 32, single_sample: int = 16, tol: float = 5e-3,
+                  target: float = 1e-2):
     """The learned surrogate on 1-D tubes of L nodes (workloads.surrogate_tubes:
     gamma in {5/3, 1.4, 9/7, 1.25}, pressure ratio log-U[2,100], density ratio
     U[1,10], tau 0.8, FD transport m = 10).  Training pairs: restarted-method
@@ -440,6 +441,7 @@ def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int =
         s.close()
     q = lambda v, p: float(np.percentile(v, p)) if v.size else None
     within = float((e_sur <= tol).sum() / max(1, e_all.size))
+    within_target = float((e_sur <= target).sum() / max(1, e_all.size))
     return {"metric": "surrogate speedup vs single-instance method at the measured rollout L1",
             "value": single_ms / sur_ms, "unit": "x",
             "config": f"{eval_tubes} held-out tubes x {L} nodes, K = {K} steps per call, "
@@ -452,7 +454,9 @@ def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int =
             # speedup holds at the rollout accuracy reported beside it
             "per_call_check_tol": tol,
             "speedup_at": {"rollout_l1_p95": q(e_sur, 95), "rollout_l1_max": q(e_sur, 100),
-                           "fraction_of_scored_tubes_within_tol": within},
+                           "fraction_of_scored_tubes_within_tol": within,
+                           "rollout_target": target,
+                           "fraction_of_scored_tubes_within_target": within_target},
             "l1_vs_method_after_rollout": {"median": q(e_sur, 50), "p95": q(e_sur, 95),
                                            "max": q(e_sur, 100), "tubes": int(ok.sum()),
                                            "within_tol": within,
@@ -991,8 +995,9 @@ def main():
     ap.add_argument("--surrogate-windows", type=int, default=125)
     ap.add_argument("--surrogate-seconds", type=float, default=60.0)
     ap.add_argument("--surrogate-patch", type=int, default=4)
-    ap.add_argument("--surrogate-tol", type=float, default=1e-2,
-                    help="per-call tolerance of the surrogate's checks")
+    ap.add_argument("--surrogate-tol", type=float, default=5e-3,
+                    help="per-call tolerance of the surrogate's checks (half the rollout's "
+                         "1e-2 target: the checks bound each call, not the accumulated error)")
     ap.add_argument("--conv-impl", type=int, default=3,
                     help="convolution kernel for --only conv (include/lbm.h impl codes)")
     ap.add_argument("--batched-count", type=int, default=4096)
