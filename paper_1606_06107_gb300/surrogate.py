@@ -547,7 +547,7 @@ class SurrogateRunner:
     (CUDA events, milliseconds).
     """
 
-    def __init__(self, net: ConvOperator, n, tau, L, K, tol=1e-2, window=256, m_fd=10,
+    def __init__(self, net: ConvOperator, n, tau, L, K, tol=5e-3, window=256, m_fd=10,
                  timing=False, fallback_window=512):
         import torch
         self.net, self.torch = net, torch
