@@ -189,11 +189,11 @@ def oracle_timing(budget: float = 8.0):
 
 
 def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
-                sample_steps: int = 200):
+                sample_steps: int = 200, mode: str = "fd"):
     """The ensemble workload: `count` 1-D shock tubes of uneven length
     (U{256..8192}), gamma in {5/3, 1.4, 9/7, 1.25}, pressure ratio log-U[2,100],
-    density ratio U[1,10], tau U[0.55,1.0], FD transport (m = 10), advanced by
-    one persistent graph-launched kernel for `steps` steps.  The speedup is
+    density ratio U[1,10], tau U[0.55,1.0], FD transport (m = 10; or STREAM,
+    `mode`), advanced by one persistent graph-launched kernel for `steps` steps.  The speedup is
     against running the same tubes one lbm_handle at a time (lbm_step
     launches), measured on a length-stratified sample of `sample` tubes and
     scaled to the ensemble; the accuracy statement is the largest rel-L1
@@ -209,7 +209,7 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
     u = np.concatenate([w.u[0] for w in wls])
     T = np.concatenate([w.T for w in wls])
     stream = torch.cuda.current_stream()
-    b = LbmBatch(lengths, [w.n for w in wls], [w.tau for w in wls], mode="fd", m_fd=10,
+    b = LbmBatch(lengths, [w.n for w in wls], [w.tau for w in wls], mode=mode, m_fd=10,
                  device=dev, stream=stream)
     b.set_macro(rho, u, T)
     threads, bps = b.autotune(20)
@@ -234,7 +234,7 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
     order = np.argsort(lengths)
     pick = order[np.linspace(0, count - 1, sample).astype(int)]
     bs = LbmBatch(lengths[pick], [wls[k].n for k in pick], [wls[k].tau for k in pick],
-                  mode="fd", m_fd=10, device=dev, stream=stream)
+                  mode=mode, m_fd=10, device=dev, stream=stream)
     bs.set_block(threads, bps)
     rs = np.concatenate([wls[k].rho for k in pick])
     us = np.concatenate([wls[k].u[0] for k in pick])
@@ -245,7 +245,7 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
     single_s, worst = 0.0, 0.0
     for j, k in enumerate(pick):
         w = wls[k]
-        s = Lbm("D1Q7", w.n, w.tau, w.shape, ("copy",), mode="fd", m_fd=10, device=dev,
+        s = Lbm("D1Q7", w.n, w.tau, w.shape, ("copy",), mode=mode, m_fd=10, device=dev,
                 stream=stream)
         s.set_macro(w.rho, w.u, w.T)
         s.step(2)
@@ -265,7 +265,9 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
         s.close()
     plain_time = single_s * (count / sample) * steps
     return {"metric": "Mnode-updates/s (f+g), ensemble", "value": value,
-            "unit": "Mnode-updates/s", "tubes": count, "nodes": total, "steps": steps,
+            "unit": "Mnode-updates/s", "mode": mode,
+            "physical_time_per_step": (0.1 if mode == "fd" else 1.0),  # in units of dx / r
+            "tubes": count, "nodes": total, "steps": steps,
             "ms_total": dt * 1e3, "threads_per_block": threads,
             "blocks_per_sm": bps, "launches": launches,
             "stable_fraction": 1.0 - bad / count,
@@ -814,7 +816,7 @@ def run_gpu(args):
     if args.only != "all":  # one leg alone, at the given size (profiling runs)
         if args.only == "batched":
             res = batched_leg(dev, steps=args.batched_steps, count=args.batched_count,
-                              sample=min(48, args.batched_count))
+                              sample=min(48, args.batched_count), mode=args.batched_mode)
         elif args.only == "conv":
             res = conv_leg(dev, tubes=args.surrogate_eval_tubes, impl=args.conv_impl)
         elif args.only == "surrogate":
@@ -921,6 +923,11 @@ def run_gpu(args):
     batched = None
     if world == 1 and not args.no_batched:
         batched = batched_leg(dev, steps=args.batched_steps, count=args.batched_count)
+        # the same tubes over the same physical time with STREAM transport
+        # (one lattice step = 10 FD sub-steps): a tenth of the node updates,
+        # but only the tubes within STREAM's shock envelope stay finite
+        batched["stream_same_physical_time"] = batched_leg(
+            dev, steps=args.batched_steps // 10, count=args.batched_count, mode="stream")
     storage = None
     if world == 1 and not args.no_storage:
         storage = storage_leg(dev, size=X, steps=args.storage_steps,
@@ -1002,6 +1009,8 @@ def main():
                     help="convolution kernel for --only conv (include/lbm.h impl codes)")
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--batched-steps", type=int, default=4000)
+    ap.add_argument("--batched-mode", default="fd", choices=["fd", "stream"],
+                    help="transport of the ensemble for --only batched")
     ap.add_argument("--blast-size", type=int, default=384)
     ap.add_argument("--blast-steps", type=int, default=10)
     ap.add_argument("--blast-oracle-size", type=int, default=64,
