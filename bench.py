@@ -264,6 +264,27 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
                 worst = max(worst, float(np.abs(e[sl] - r).sum() / den))
         s.close()
     plain_time = single_s * (count / sample) * steps
+    # the ensemble against the FP64 oracle on the shortest sampled tubes
+    from oracle import oracle
+    orc_err = {"rho": 0.0, "u": 0.0, "T": 0.0}
+    compared = 0
+    for j, k in enumerate(pick[:8]):
+        if compared == 4:
+            break
+        w = wls[k]
+        ref = oracle.Sim(oracle.D1Q7, w.n, w.tau, w.shape, (oracle.COPY,),
+                         mode=oracle.FD if mode == "fd" else oracle.STREAM, m_fd=10)
+        ref.set_macro(w.rho, w.u, w.T)
+        ref.step(sample_steps)
+        want = ref.moments()
+        if not all(np.all(np.isfinite(x)) for x in want):
+            continue
+        sl = slice(bs.offsets[j], bs.offsets[j] + lengths[k])
+        for name, e, r in zip(("rho", "u", "T"), ens, want):
+            r = np.asarray(r, dtype=np.float64).reshape(-1)
+            orc_err[name] = max(orc_err[name],
+                                float(np.abs(e[sl].astype(np.float64) - r).sum() / np.abs(r).sum()))
+        compared += 1
     return {"metric": "Mnode-updates/s (f+g), ensemble", "value": value,
             "unit": "Mnode-updates/s", "mode": mode,
             "physical_time_per_step": (0.1 if mode == "fd" else 1.0),  # in units of dx / r
@@ -274,7 +295,10 @@ def batched_leg(dev, steps: int = 4000, count: int = 4096, sample: int = 48,
             "speedup_vs_per_tube_launches": plain_time / dt,
             "per_tube_baseline": f"{sample} length-stratified tubes x {sample_steps} lbm_step "
                                  f"launches each, scaled to {count} tubes x {steps} steps",
-            "rel_l1_vs_per_tube": worst}
+            "rel_l1_vs_per_tube": worst,
+            "rel_l1_vs_fp64_oracle": dict(orc_err, sample=f"max over the {compared} shortest "
+                                                          f"finite sampled tubes after "
+                                                          f"{sample_steps} steps")}
 
 
 def surrogate_leg(dev, train_tubes: int = 1600, eval_tubes: int = 1024, L: int = 4096,
@@ -965,6 +989,11 @@ def run_gpu(args):
                      "traffic": NCU_TRAFFIC_BYTES, "kernel": "k_step<D2Q49,rot,STREAM>",
                      "avg_launch_ms": avg_launch * 1e3},
         "cpu_baseline": cpu,
+        # error of this float32 step against the FP64 oracle: the storage
+        # leg's float row (the same recipe at 256^2 after 100 steps)
+        "rel_l1_vs_fp64_oracle": (dict(storage["f32"]["rel_l1_vs_fp64_oracle"],
+                                       sample=storage["error_sample"])
+                                  if storage and "f32" in storage else None),
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks.summary(),
