@@ -27,7 +27,9 @@
 // loads and stores (17 % fewer instructions per node but 168 registers, so
 // 11 resident warps per SM instead of 19, 30 % slower); one pointer per
 // source column with block-uniform row offsets (5 % more instructions than
-// integer offsets).
+// integer offsets); the block's 7 x 134 source records staged in shared
+// memory once instead of each value loading its record from L1 (6.8 against
+// 7.8 Gnode/s: the barrier and the staging cost more than the L1 hits).
 #pragma once
 
 // Resident 128-thread blocks per SM the register allocation must allow
