@@ -710,7 +710,7 @@ def dist_setup(n_gpus):
 
 
 def blast_storage_crop(dev, L: int = 384, steps: int = 500, crop: int = 64, n: int = 0,
-                       chunk: int = 0):
+                       chunk: int = 0, p_in: float = 1.5, p_out: float = 0.5):
     """Storage error of the 3-D blast: the same L^3 problem run with f16
     deviation storage and with float storage (2 x 79 GB of state), compared
     on the central crop^3 nodes (rel-L1 of rho, T and of u against the
@@ -726,7 +726,7 @@ def blast_storage_crop(dev, L: int = 384, steps: int = 500, crop: int = 64, n: i
     chunk = chunk or max(1, steps // 10)
     crops, out = {}, {}
     for storage in ("f16", "f32"):
-        wl = workloads.blast_3d(L=L, radius=32 * L / 384, n=n, p_in=1.5, p_out=0.5)
+        wl = workloads.blast_3d(L=L, radius=32 * L / 384, n=n, p_in=p_in, p_out=p_out)
         g = Lbm("D3Q343", n, 2 / 3, (L, L, L), ("periodic",) * 3, device=dev, storage=storage)
         g.set_macro(wl.rho, wl.u, wl.T)
         del wl
@@ -765,7 +765,7 @@ def blast_storage_crop(dev, L: int = 384, steps: int = 500, crop: int = 64, n: i
             "rho": float(np.abs(r16 - r32).sum() / np.abs(r32).sum()),
             "u": float(np.abs(u16 - u32).sum() / (3 * cs.sum())),
             "T": float(np.abs(t16 - t32).sum() / np.abs(t32).sum())}
-    out["config"] = (f"blast_3d {L}^3 D3Q343 n={n}, stable-envelope variant p 1.5 | 0.5, "
+    out["config"] = (f"blast_3d {L}^3 D3Q343 n={n}, p {p_in} | {p_out}, "
                      f"up to {steps} steps in chunks of {chunk}, central {crop}^3 crop")
     return out
 
@@ -860,7 +860,9 @@ def run_gpu(args):
             if args.blast_crop_steps > 0:
                 res["storage_error_crop"] = blast_storage_crop(dev, L=args.blast_size,
                                                                steps=args.blast_crop_steps,
-                                                               crop=min(64, args.blast_size))
+                                                               crop=min(64, args.blast_size),
+                                                               p_in=args.blast_p_in,
+                                                               p_out=args.blast_p_out)
         print(json.dumps(res), flush=True)
         return
     if world > 1:
@@ -1042,6 +1044,10 @@ def main():
                     help="transport of the ensemble for --only batched")
     ap.add_argument("--blast-size", type=int, default=384)
     ap.add_argument("--blast-steps", type=int, default=10)
+    ap.add_argument("--blast-p-in", type=float, default=1.5,
+                    help="sphere pressure of --blast-crop-steps' problem")
+    ap.add_argument("--blast-p-out", type=float, default=0.5,
+                    help="background pressure of --blast-crop-steps' problem")
     ap.add_argument("--blast-oracle-size", type=int, default=64,
                     help="edge of the scaled blast problem compared with the FP64 oracle")
     ap.add_argument("--blast-oracle-steps", type=int, default=60,
