@@ -123,3 +123,44 @@ def test_batch_create_validation_and_sizes(lbmlib):
         assert lbmlib.lbm_batch_set_watch(h, None, None) == 0                   # whole problems
     finally:
         lbmlib.lbm_batch_destroy(h)
+
+
+def test_node_reference_storage_sizes_and_limits(lbmlib):
+    """Per-node reference storage (LBM_STORE_F16_NODE = 3, BF16_NODE = 4):
+    the state buffer holds the 16-bit populations, then, 256-byte aligned, one
+    16-byte record per node; STREAM on the 1-D and 2-D lattices only.  Host
+    calls only."""
+    sb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+    shape = (ctypes.c_int64 * 3)(100, 10, 1)
+    bc = (ctypes.c_int * 3)(0, 0, 0)
+    for storage, rest in ((3, 1), (4, 2)):
+        sizes = {}
+        for st in (storage, rest):
+            rc, h = _create(lbmlib, 2, 3, 3, 2 / 3)  # D2Q49 + D1Q7
+            assert rc == 0
+            try:
+                assert lbmlib.lbm_set_storage(h, st) == 0
+                assert lbmlib.lbm_set_grid(h, shape, bc, ctypes.byref(sb), ctypes.byref(wb)) == 0
+                sizes[st] = sb.value
+            finally:
+                lbmlib.lbm_destroy(h)
+        S = 128 * 10  # pitch of 100 halves rounded up to 64, times Y
+        assert sizes[rest] == 2 * 56 * S
+        assert sizes[storage] == (2 * 56 * S + 255) // 256 * 256 + 16 * S
+    # FD transport and D3Q343 are refused at lbm_set_grid
+    rc, h = _create(lbmlib, 1, 1, 4, 2 / 3)
+    try:
+        assert lbmlib.lbm_set_mode(h, 1, 10) == 0
+        assert lbmlib.lbm_set_storage(h, 3) == 0
+        assert lbmlib.lbm_set_grid(h, (ctypes.c_int64 * 3)(64, 1, 1), bc, ctypes.byref(sb),
+                                   ctypes.byref(wb)) == -1
+    finally:
+        lbmlib.lbm_destroy(h)
+    rc, h = _create(lbmlib, 3, 4, 0, 2 / 3)
+    try:
+        assert lbmlib.lbm_set_storage(h, 4) == 0
+        assert lbmlib.lbm_set_grid(h, (ctypes.c_int64 * 3)(8, 8, 8), bc, ctypes.byref(sb),
+                                   ctypes.byref(wb)) == -1
+        assert lbmlib.lbm_set_storage(h, 5) == -1  # unknown storage
+    finally:
+        lbmlib.lbm_destroy(h)
