@@ -8,6 +8,10 @@ workloads.riemann_2d_wide; the stated draws go non-finite).  A step is one fused
 launch over all nodes.  The state (2 x 940 MB) is larger than L2, so no flush
 is needed between steps.
 
+The same JSON line carries further legs (each skippable with --no-*/--only):
+the same step with 16-bit population storages, many uneven 1-D tubes in one
+persistent launch, the 3-D D3Q343 blast, and the learned surrogate.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU runs (torchrun) are independent replicas, one per GPU.
 """

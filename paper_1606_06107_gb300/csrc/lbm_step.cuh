@@ -11,9 +11,11 @@
 //
 // The step is memory bound: every population is read once and written once
 // per step; all moments and equilibria live in registers.  Populations are
-// stored as float, or as __half / __nv_bfloat16 deviations (Storage below);
-// every kernel is instantiated per storage type.  One thread owns
-// one node; a block is 128 consecutive x positions of one row.
+// stored as float, as __half / __nv_bfloat16 deviations from rest (Storage
+// below), or as deviations from a per-node reference (NodeHalf / NodeBf16,
+// with a record per node after the populations; their step kernel is in
+// lbm_step_node.cuh); every kernel is instantiated per storage type.  One
+// thread owns one node; a block is 128 consecutive x positions of one row.
 #pragma once
 #include <cstdint>
 #include <type_traits>

@@ -158,7 +158,10 @@ class Lbm:
     Parameters follow include/lbm.h: ``lattice`` in LATTICES, ``n`` rotational
     degrees of freedom, ``tau`` relaxation time in lattice steps, ``shape``
     (X,), (X, Y) or (X, Y, Z) with x fastest, ``bc`` per axis in BCS,
-    ``mode`` "stream" or "fd" (with ``m_fd`` sub-steps).
+    ``mode`` "stream" or "fd" (with ``m_fd`` sub-steps), ``storage`` in
+    STORAGES: "f32"; "f16" / "bf16" deviations from the rest equilibrium;
+    "f16_node" / "bf16_node" deviations from each node's own reference
+    equilibrium (STREAM mode, lattices other than D3Q343).
     """
 
     def __init__(self, lattice: str, n: int, tau: float, shape, bc, mode: str = "stream",
