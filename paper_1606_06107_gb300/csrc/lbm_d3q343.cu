@@ -66,25 +66,37 @@ __device__ __forceinline__ float decode_pop(const Params<Q, ST> &p, int pop, ST 
     else return Storage<ST>::decode(v, p.w[pop]);
 }
 
-template <bool ROT, typename ST>
-__global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(const Params<kQ343, ST> p)
+// Population i of the node at in-population offset off (64-bit element
+// index: the state of a 384^3 grid holds 2 x 10^10 values).
+template <typename ST>
+__device__ __forceinline__ ST q343_load(const Params<kQ343, ST> &p, int i, int off)
 {
-    constexpr int D = 3;
-    constexpr int C = (kQ343 - 1) / 2;  // rest velocity (171)
-    const int x = blockIdx.x * kQ343Block + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= p.X) return;
-    const Offsets o = node_offsets<D>(p, x, y, z);
-    const int plane = p.pitch * p.Y;
+    return __ldg(p.src + ((uint64_t)i * (uint64_t)p.S + (uint64_t)(uint32_t)off));
+}
+template <typename ST>
+__device__ __forceinline__ void q343_store(const Params<kQ343, ST> &p, int i, int self, float v)
+{
+    ST val;
+    if constexpr (std::is_same<ST, float>::value) val = v;
+    else val = Storage<ST>::encode(v, p.iw[i]);
+    p.dst[(uint64_t)i * (uint64_t)p.S + (uint32_t)self] = val;
+}
 
-    // pass 1: moments of the pulled populations g_i(x) = ft_i(x - e_i)
+// The five sums of pass 1: rho, j and sum_i |e_i|^2 g_i (lattice units).
+struct Q343Sums {
+    float rho, jx, jy, jz, e2;
+};
+
+// Pass 1 of one node: moments of the pulled populations g_i(x) = ft_i(x - e_i).
+// The raw values of the e_z planes c < NS are kept in the stash for pass 2.
+template <int NS, typename ST>
+__device__ __forceinline__ Q343Sums q343_sums(const Params<kQ343, ST> &p, const Offsets &o, int z, ST *stash)
+{
+    const int plane = p.pitch * p.Y;
     float cs[7];
 #pragma unroll
     for (int a = 0; a < 7; ++a) cs[a] = 0.f;
     float rho = 0.f, jy = 0.f, jz = 0.f, e2yz = 0.f;
-    extern __shared__ unsigned char q343_smem[];
-    ST *stash = reinterpret_cast<ST *>(q343_smem);  // [NS planes x 49][kQ343Block] raw values
-    constexpr int NS = StashPlanes<ST>::value;
     // e_y is unrolled so that each e_z plane issues its 49 loads at once
     auto plane1 = [&](auto keep, int c) {
         constexpr bool KEEP = decltype(keep)::value;
@@ -96,7 +108,7 @@ __global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(c
 #pragma unroll
             for (int a = 0; a < 7; ++a) {
                 const int i = (c * 7 + b) * 7 + a;
-                const ST v = __ldg(p.src + ((uint64_t)i * (uint64_t)p.S + (uint64_t)(uint32_t)(row + o.x[6 - a])));
+                const ST v = q343_load(p, i, row + o.x[6 - a]);
                 if constexpr (KEEP) stash[i * kQ343Block + threadIdx.x] = v;
                 const float g = decode_pop(p, i, v);
                 cs[a] += g;
@@ -119,6 +131,19 @@ __global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(c
         jx = fmaf((float)k, cs[3 + k] - cs[3 - k], jx);
         e2 = fmaf((float)(k * k), cs[3 + k] + cs[3 - k], e2);
     }
+    return Q343Sums{rho, jx, jy, jz, e2};
+}
+
+// Pass 2 of one node and the rotational update: moments, equilibrium, BGK,
+// store (the rest and the unit velocities deferred).  The values of the e_z
+// planes c < NS come from the stash, the others are pulled again.
+template <bool ROT, int NS, typename ST>
+__device__ __forceinline__ void q343_collide(const Params<kQ343, ST> &p, const Offsets &o, int z,
+                                             const Q343Sums &s, const ST *stash)
+{
+    constexpr int D = 3;
+    constexpr int C = (kQ343 - 1) / 2;  // rest velocity (171)
+    const int plane = p.pitch * p.Y;
     float h[7], R2 = 0.f;
     if (ROT) {
 #pragma unroll
@@ -126,10 +151,9 @@ __global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(c
 #pragma unroll
         for (int k = 1; k <= 3; ++k) R2 = fmaf((float)(k * k), h[3 + k] + h[3 - k], R2);
     }
-    const Moments m = make_moments<D, ROT>(p, rho, jx, jy, jz, e2, R2);
+    const Moments m = make_moments<D, ROT>(p, s.rho, s.jx, s.jy, s.jz, s.e2, R2);
     if (!(m.rho > 0.f) || !(m.T > 0.f) || !(fabsf(m.T) < 3.0e38f)) atomicOr(p.status, 1);
 
-    // pass 2: equilibrium, BGK, store (rest and unit velocities deferred)
     const float u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
     const float om_rho = p.omega * m.rho;
     const EqCoef k = eq_coef<D>(m.T, u2, om_rho);  // omega rho g^eq / w_i
@@ -166,7 +190,7 @@ __global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(c
                 if (ex) rx = fmaf((float)ex, q, rx);
                 float g;
                 if constexpr (KEPT) g = decode_pop(p, i, stash[i * kQ343Block + threadIdx.x]);
-                else g = ld(p, i, row + o.x[6 - a]);
+                else g = decode_pop(p, i, q343_load(p, i, row + o.x[6 - a]));
                 if (E2 <= 1) {  // the rest and the six unit velocities: stored last
                     if (E2 == 0) { q_c = q; g_c = g; }
                     else if (ex == -1) { q_mx = q; g_mx = g; }
@@ -176,7 +200,7 @@ __global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(c
                     else if (ez == -1) { q_mz = q; g_mz = g; }
                     else { q_pz = q; g_pz = g; }
                 } else {
-                    st(p, i, self, fmaf(keep, g, q));
+                    q343_store(p, i, self, fmaf(keep, g, q));
                 }
             }
             p0 += r0;
@@ -200,19 +224,34 @@ __global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(c
     const float dmx = 0.5f * (p.omega * m.j[0] - ax);
     const float dmy = 0.5f * (p.omega * m.j[1] - ay);
     const float dmz = 0.5f * (p.omega * m.j[2] - az);
-    st(p, C, self, fmaf(keep, g_c, q_c + (d0 - d2)));
-    st(p, C - 1, self, fmaf(keep, g_mx, q_mx + (bb - dmx)));
-    st(p, C + 1, self, fmaf(keep, g_px, q_px + (bb + dmx)));
-    st(p, C - 7, self, fmaf(keep, g_my, q_my + (bb - dmy)));
-    st(p, C + 7, self, fmaf(keep, g_py, q_py + (bb + dmy)));
-    st(p, C - 49, self, fmaf(keep, g_mz, q_mz + (bb - dmz)));
-    st(p, C + 49, self, fmaf(keep, g_pz, q_pz + (bb + dmz)));
+    q343_store(p, C, self, fmaf(keep, g_c, q_c + (d0 - d2)));
+    q343_store(p, C - 1, self, fmaf(keep, g_mx, q_mx + (bb - dmx)));
+    q343_store(p, C + 1, self, fmaf(keep, g_px, q_px + (bb + dmx)));
+    q343_store(p, C - 7, self, fmaf(keep, g_my, q_my + (bb - dmy)));
+    q343_store(p, C + 7, self, fmaf(keep, g_py, q_py + (bb + dmy)));
+    q343_store(p, C - 49, self, fmaf(keep, g_mz, q_mz + (bb - dmz)));
+    q343_store(p, C + 49, self, fmaf(keep, g_pz, q_pz + (bb + dmz)));
 
     if (ROT) {
         float adv[7];
         rot_advect<D>(p, o, h, m, adv);
         rot_store(p, self, h, m, adv);
     }
+}
+
+// One launch: pass 1, then pass 2 on the same thread.
+template <bool ROT, typename ST>
+__global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(const Params<kQ343, ST> p)
+{
+    const int x = blockIdx.x * kQ343Block + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.X) return;
+    const Offsets o = node_offsets<3>(p, x, y, z);
+    extern __shared__ unsigned char q343_smem[];
+    ST *stash = reinterpret_cast<ST *>(q343_smem);  // [NS planes x 49][kQ343Block] raw values
+    constexpr int NS = StashPlanes<ST>::value;
+    const Q343Sums s = q343_sums<NS>(p, o, z, stash);
+    q343_collide<ROT, NS>(p, o, z, s, stash);
 }
 
 }  // namespace
