@@ -27,7 +27,14 @@
 
 namespace lbm {
 
-constexpr int kBlockX = 128;
+// Threads per block (x positions of one row).  On the 2048^2 D2Q49 float
+// step, with the register cap held at 128 by the resident-block count:
+// 128 threads 12,855 Mnode/s, 64 at 8 blocks 12,806, 256 at 2 12,714, 512
+// at 1 10,502.
+#ifndef LBM_BLOCK_X
+#define LBM_BLOCK_X 128
+#endif
+constexpr int kBlockX = LBM_BLOCK_X;
 
 // Minimum resident blocks per SM requested from the compiler for the step
 // kernel, by storage type.  float: 4 caps the D2Q49 kernel at 128 registers
