@@ -6,7 +6,8 @@
 // sums by (e_y, e_z), column sums by e_x), a second pass re-reads each value
 // (from a shared-memory stash for the first planes with 16-bit storage, else
 // from L1/L2: a 128-node block touches 343 x 128 x 4 B = 175 KB between the
-// two reads) and writes its post-collision value.  The second pass walks the
+// two reads) and writes its post-collision value (with 16-bit storage as a
+// deviation computed from the stored deviation, below).  The second pass walks the
 // e_z planes in reverse, so that it starts on the lines the first pass loaded
 // last, which are the ones still in L1 (7 % faster with float storage, 1 %
 // with f16).  The rest and the six unit
@@ -24,22 +25,25 @@ constexpr int kQ343 = 343;
 
 // Resident blocks per SM the register allocation must allow.  Left free the
 // compiler takes 185-207 registers (2 blocks of 4 warps); 3 blocks (at most
-// 170 registers, 0-20 bytes of spill) measured 13 % (n = 0) and 7 % (n = 4) faster on
-// the 384^3 f16 blast, 4 and 5 blocks spill and are slower.
+// 170 registers, 0-60 bytes of spill) measured 13 % (n = 0) and 7 % (n = 4)
+// faster on the 384^3 f16 blast; 4 blocks (128 registers, at most 4 stash
+// planes in the shared memory) are slower: 33.9 / 42.1 ms with 4 planes,
+// 36.3 / 44.7 with 3, against 31.0 / 35.0 at 3 blocks with 5.
 #ifndef LBM_Q343_MIN_BLOCKS
 #define LBM_Q343_MIN_BLOCKS 3
 #endif
 // Shared-memory stash of the first pass's raw values for the e_z planes
 // c < NS, which the second pass (walking the planes in reverse) reaches
-// last, when L1 has long evicted them.  6 planes of 16-bit values take
-// 75.3 KB per 128-thread block (3 blocks per SM still fit) and made the
-// 384^3 f16 blast 9 % (n = 0) and 8 % (n = 4) faster (ms per step, n = 0 /
-// n = 4: none 36.2 / 42.2, 4 planes 35.2 / 41.3, 5 33.3 / 39.4, 6 33.0 /
-// 38.8, all 7 at 2 blocks per SM 43.9 / 46.9); float storage gained nothing
-// from 2 planes.  The second pass decodes the same stored bits, so results
-// are unchanged.
+// last, when L1 has long evicted them.  16-bit values take 12.5 KB per plane
+// per 128-thread block.  With the deviation-form pass 2 below, on the 384^3
+// f16 blast (ms per step, n = 0 / n = 4): 4 planes 32.6 / 36.2, 5 planes
+// 31.0 / 35.0, 6 planes 32.6 / 36.5 (with the weight-table pass 2 6 planes
+// had been best: none 36.2 / 42.2, 4 35.2 / 41.3, 5 33.3 / 39.4, 6 33.0 /
+// 38.8, all 7 at 2 blocks per SM 43.9 / 46.9).  Float storage gained nothing
+// from 2 planes.  The second pass decodes the same stored bits, so the depth
+// does not change results.
 #ifndef LBM_Q343_STASH_HALF
-#define LBM_Q343_STASH_HALF 6
+#define LBM_Q343_STASH_HALF 5
 #endif
 #ifndef LBM_Q343_STASH_FLOAT
 #define LBM_Q343_STASH_FLOAT 0
@@ -80,6 +84,40 @@ __device__ __forceinline__ void q343_store(const Params<kQ343, ST> &p, int i, in
     if constexpr (std::is_same<ST, float>::value) val = v;
     else val = Storage<ST>::encode(v, p.iw[i]);
     p.dst[(uint64_t)i * (uint64_t)p.S + (uint32_t)self] = val;
+}
+
+// Pass 2 with 16-bit deviation storage, d_i = f_i / w_i - 1, runs on the
+// deviations with the weights factored.  D3Q343 = D1Q7^3, so w_i = w_a w_b
+// w_c.  The e_z planes c are a run-time loop, so a table lookup w[i] (or
+// 1 / w[i]) is a run-time-indexed parameter load for every population; here
+// the in-plane factors w_a w_b, w_a w_b e_x and w_a w_b e_x^2 (compile-time
+// indices inside the unrolled row) are immediate operands of the row sums and
+// the plane factor w_c multiplies the plane sums once.  The collision
+// f* = (1 - omega) g + omega g^eq becomes d* = (1 - omega) d + (P - omega)
+// with P = omega rho g^eq / w, so no value is decoded to f or encoded back.
+// Measured on the 384^3 f16 blast (ms per step, n = 0 / n = 4, 6 stash
+// planes): 33.7 / 40.1 with the weight table, 32.6 / 36.5 in this form; the
+// same treatment of pass 1 (weighted deviation sums scaled by w_c per row)
+// took 35.4 / 45.0 alone and 36.5 / 40.2 with both (more registers, spills);
+// with 5 stash planes, 30.8 / 36.2 with both against 31.1 / 35.2 for pass 2
+// alone.
+#ifndef LBM_Q343_DEV
+#define LBM_Q343_DEV 1
+#endif
+struct Q343Weights {
+    float w2[49];    // w_a w_b, index b * 7 + a
+    float w2x[49];   // w_a w_b e_x
+    float w2x2[49];  // w_a w_b e_x^2
+    float wc[7];     // w_c
+    float iw_rest, iw_unit;  // 1 / w of the rest velocity and of the unit velocities
+};
+template <typename ST> struct Q343Dev {
+    static constexpr bool value = LBM_Q343_DEV && !std::is_same<ST, float>::value;
+};
+template <typename ST>
+__device__ __forceinline__ void q343_store_dev(const Params<kQ343, ST> &p, int i, int self, float d)
+{
+    p.dst[(uint64_t)i * (uint64_t)p.S + (uint32_t)self] = Storage<ST>::from_dev(d);
 }
 
 // The five sums of pass 1: rho, j and sum_i |e_i|^2 g_i (lattice units).
@@ -239,9 +277,120 @@ __device__ __forceinline__ void q343_collide(const Params<kQ343, ST> &p, const O
     }
 }
 
+// Pass 2 for 16-bit deviation storage (the factored-weight form above).
+// Same structure as q343_collide: row and plane sums of w_i P_i, w_i |e_i|^2
+// P_i and w_i e_i P_i, which are the sums of the post-collision equilibrium
+// part q_i = w_i P_i, and the float32 corrections put on the rest and unit
+// velocities (divided by their weights, since those are stored as
+// deviations).
+template <bool ROT, int NS, typename ST>
+__device__ __forceinline__ void q343_collide_dev(const Params<kQ343, ST> &p, const Q343Weights &qw, const Offsets &o,
+                                                 int z, const Q343Sums &s, const ST *stash)
+{
+    constexpr int D = 3;
+    constexpr int C = (kQ343 - 1) / 2;  // rest velocity (171)
+    const int plane = p.pitch * p.Y;
+    float h[7], R2 = 0.f;
+    if (ROT) {
+#pragma unroll
+        for (int j = 0; j < 7; ++j) h[j] = ld(p, kQ343 + j, o.self());
+#pragma unroll
+        for (int k = 1; k <= 3; ++k) R2 = fmaf((float)(k * k), h[3 + k] + h[3 - k], R2);
+    }
+    const Moments m = make_moments<D, ROT>(p, s.rho, s.jx, s.jy, s.jz, s.e2, R2);
+    if (!(m.rho > 0.f) || !(m.T > 0.f) || !(fabsf(m.T) < 3.0e38f)) atomicOr(p.status, 1);
+
+    const float u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    const float om_rho = p.omega * m.rho;
+    const EqCoef k = eq_coef<D>(m.T, u2, om_rho);  // P_i = omega rho g^eq_i / w_i
+    const float keep = 1.0f - p.omega;
+    const float rux = m.ux * p.r, ruy = m.uy * p.r, ruz = m.uz * p.r;
+    const int self = o.self();
+    float acc0 = 0.f, acc2 = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+    float P_c = 0.f, P_mx = 0.f, P_px = 0.f, P_my = 0.f, P_py = 0.f, P_mz = 0.f, P_pz = 0.f;
+    float d_c = 0.f, d_mx = 0.f, d_px = 0.f, d_my = 0.f, d_py = 0.f, d_mz = 0.f, d_pz = 0.f;
+    auto plane2 = [&](auto kept, int c) {
+        constexpr bool KEPT = decltype(kept)::value;
+        const int zo = bc_wrap(z - (c - 3), p.Z, p.bc2) * plane;
+        const int ez = c - 3;
+        const float ez2 = (float)(ez * ez);
+        float p0 = 0.f, p2 = 0.f, px = 0.f, py = 0.f;  // plane sums (without w_c)
+#pragma unroll
+        for (int b = 0; b < 7; ++b) {
+            const int row = zo + o.y[6 - b];
+            const int ey = b - 3;
+            const float cyz = fmaf((float)ey, ruy, (float)ez * ruz);
+            const float eyz2 = (float)(ey * ey) + ez2;
+            const float syz = p.r2 * eyz2;
+            float r0 = 0.f, r2 = 0.f, rx = 0.f;  // row sums (without w_c)
+#pragma unroll
+            for (int a = 0; a < 7; ++a) {
+                const int ex = a - 3;
+                const int i = (c * 7 + b) * 7 + a;
+                const float cdot = fmaf((float)ex, rux, cyz);
+                const float P = eq_single(k, cdot, fmaf(p.r2, (float)(ex * ex), syz));
+                r0 = fmaf(qw.w2[b * 7 + a], P, r0);
+                if (ex) {
+                    r2 = fmaf(qw.w2x2[b * 7 + a], P, r2);
+                    rx = fmaf(qw.w2x[b * 7 + a], P, rx);
+                }
+                float d;
+                if constexpr (KEPT) d = Storage<ST>::to_dev(stash[i * kQ343Block + threadIdx.x]);
+                else d = Storage<ST>::to_dev(q343_load(p, i, row + o.x[6 - a]));
+                if (ex * ex + ey * ey + ez * ez <= 1) {  // the rest and the six unit velocities: stored last
+                    if (ex == 0 && ey == 0 && ez == 0) { P_c = P; d_c = d; }
+                    else if (ex == -1) { P_mx = P; d_mx = d; }
+                    else if (ex == 1) { P_px = P; d_px = d; }
+                    else if (ey == -1) { P_my = P; d_my = d; }
+                    else if (ey == 1) { P_py = P; d_py = d; }
+                    else if (ez == -1) { P_mz = P; d_mz = d; }
+                    else { P_pz = P; d_pz = d; }
+                } else {
+                    q343_store_dev(p, i, self, fmaf(keep, d, P - p.omega));
+                }
+            }
+            p0 += r0;
+            p2 += fmaf(eyz2, r0, r2);
+            px += rx;
+            py = fmaf((float)ey, r0, py);
+        }
+        const float wc = qw.wc[c];
+        acc0 = fmaf(wc, p0, acc0);
+        acc2 = fmaf(wc, p2, acc2);
+        ax = fmaf(wc, px, ax);
+        ay = fmaf(wc, py, ay);
+        az = fmaf(wc * (float)ez, p0, az);
+    };
+    for (int c = 6; c >= 0; --c) {
+        if (c < NS) plane2(std::true_type{}, c);
+        else plane2(std::false_type{}, c);
+    }
+    const float d0 = om_rho - acc0;
+    const float d2 = p.omega * m.E2_eq - acc2;
+    const float bb = d2 * (0.5f / (float)D);
+    const float dmx = 0.5f * (p.omega * m.j[0] - ax);
+    const float dmy = 0.5f * (p.omega * m.j[1] - ay);
+    const float dmz = 0.5f * (p.omega * m.j[2] - az);
+    const float iw0 = qw.iw_rest, iw1 = qw.iw_unit;
+    q343_store_dev(p, C, self, fmaf(keep, d_c, fmaf(d0 - d2, iw0, P_c - p.omega)));
+    q343_store_dev(p, C - 1, self, fmaf(keep, d_mx, fmaf(bb - dmx, iw1, P_mx - p.omega)));
+    q343_store_dev(p, C + 1, self, fmaf(keep, d_px, fmaf(bb + dmx, iw1, P_px - p.omega)));
+    q343_store_dev(p, C - 7, self, fmaf(keep, d_my, fmaf(bb - dmy, iw1, P_my - p.omega)));
+    q343_store_dev(p, C + 7, self, fmaf(keep, d_py, fmaf(bb + dmy, iw1, P_py - p.omega)));
+    q343_store_dev(p, C - 49, self, fmaf(keep, d_mz, fmaf(bb - dmz, iw1, P_mz - p.omega)));
+    q343_store_dev(p, C + 49, self, fmaf(keep, d_pz, fmaf(bb + dmz, iw1, P_pz - p.omega)));
+
+    if (ROT) {
+        float adv[7];
+        rot_advect<D>(p, o, h, m, adv);
+        rot_store(p, self, h, m, adv);
+    }
+}
+
 // One launch: pass 1, then pass 2 on the same thread.
 template <bool ROT, typename ST>
-__global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(const Params<kQ343, ST> p)
+__global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS)
+    k_step_q343(const Params<kQ343, ST> p, const Q343Weights qw)
 {
     const int x = blockIdx.x * kQ343Block + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -251,7 +400,8 @@ __global__ void __launch_bounds__(kQ343Block, LBM_Q343_MIN_BLOCKS) k_step_q343(c
     ST *stash = reinterpret_cast<ST *>(q343_smem);  // [NS planes x 49][kQ343Block] raw values
     constexpr int NS = StashPlanes<ST>::value;
     const Q343Sums s = q343_sums<NS>(p, o, z, stash);
-    q343_collide<ROT, NS>(p, o, z, s, stash);
+    if constexpr (Q343Dev<ST>::value) q343_collide_dev<ROT, NS>(p, qw, o, z, s, stash);
+    else q343_collide<ROT, NS>(p, o, z, s, stash);
 }
 
 }  // namespace
@@ -274,7 +424,18 @@ template <bool ROT, typename ST> cudaError_t launch_step_q343(const Args &a, cud
             done[dev].store(true);
         }
     }
-    k_step_q343<ROT, ST><<<grid, kQ343Block, sh, s>>>(p);
+    Q343Weights qw;
+    for (int b = 0; b < 7; ++b)
+        for (int c = 0; c < 7; ++c) {
+            const double wab = (double)a.wr[c] * (double)a.wr[b];
+            qw.w2[b * 7 + c] = (float)wab;
+            qw.w2x[b * 7 + c] = (float)(wab * (c - 3));
+            qw.w2x2[b * 7 + c] = (float)(wab * (c - 3) * (c - 3));
+        }
+    for (int c = 0; c < 7; ++c) qw.wc[c] = a.wr[c];
+    qw.iw_rest = (float)(1.0 / ((double)a.wr[3] * (double)a.wr[3] * (double)a.wr[3]));
+    qw.iw_unit = (float)(1.0 / ((double)a.wr[2] * (double)a.wr[3] * (double)a.wr[3]));
+    k_step_q343<ROT, ST><<<grid, kQ343Block, sh, s>>>(p, qw);
     return cudaGetLastError();
 }
 

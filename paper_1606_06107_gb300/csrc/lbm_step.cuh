@@ -139,6 +139,7 @@ template <> struct Storage<__half> {
     __device__ static float decode(__half v, float w) { return fmaf(w, __half2float(v), w); }
     __device__ static __half encode(float f, float inv_w) { return __float2half_rn(fmaf(f, inv_w, -1.0f)); }
     __device__ static __half from_dev(float d) { return __float2half_rn(d); }
+    __device__ static float to_dev(__half v) { return __half2float(v); }
 };
 template <> struct Storage<__nv_bfloat16> {
     __device__ static float decode(__nv_bfloat16 v, float w)
@@ -150,6 +151,7 @@ template <> struct Storage<__nv_bfloat16> {
         return __float2bfloat16_rn(fmaf(f, inv_w, -1.0f));
     }
     __device__ static __nv_bfloat16 from_dev(float d) { return __float2bfloat16_rn(d); }
+    __device__ static float to_dev(__nv_bfloat16 v) { return __bfloat162float(v); }
 };
 
 // Per-node reference storage (LBM_STORE_F16_NODE / BF16_NODE): the same
