@@ -100,7 +100,10 @@ __device__ __forceinline__ void q343_store(const Params<kQ343, ST> &p, int i, in
 // same treatment of pass 1 (weighted deviation sums scaled by w_c per row)
 // took 35.4 / 45.0 alone and 36.5 / 40.2 with both (more registers, spills);
 // with 5 stash planes, 30.8 / 36.2 with both against 31.1 / 35.2 for pass 2
-// alone.
+// alone.  One body per pass with the stash choice a run-time predicate
+// (half the code, against the instruction-cache misses) instead of the two
+// compile-time bodies per pass: 31.0 / 35.9 (pass 1), 36.7 / 37.8 (pass 2),
+// 35.5 / 38.0 (both) against 30.9 / 35.0.
 #ifndef LBM_Q343_DEV
 #define LBM_Q343_DEV 1
 #endif
