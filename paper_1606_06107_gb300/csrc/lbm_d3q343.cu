@@ -27,8 +27,9 @@ constexpr int kQ343 = 343;
 // compiler takes 185-207 registers (2 blocks of 4 warps); 3 blocks (at most
 // 170 registers, 0-60 bytes of spill) measured 13 % (n = 0) and 7 % (n = 4)
 // faster on the 384^3 f16 blast; 4 blocks (128 registers, at most 4 stash
-// planes in the shared memory) are slower: 33.9 / 42.1 ms with 4 planes,
-// 36.3 / 44.7 with 3, against 31.0 / 35.0 at 3 blocks with 5.
+// planes in the shared memory) are slower: with the row quartic and no
+// spills 34.7 / 45.8 ms with 4 planes and 33.9 / 43.0 with 3, against 28.0
+// / 32.0 at 3 blocks with 6.
 #ifndef LBM_Q343_MIN_BLOCKS
 #define LBM_Q343_MIN_BLOCKS 3
 #endif
@@ -36,14 +37,15 @@ constexpr int kQ343 = 343;
 // c < NS, which the second pass (walking the planes in reverse) reaches
 // last, when L1 has long evicted them.  16-bit values take 12.5 KB per plane
 // per 128-thread block.  With the deviation-form pass 2 below, on the 384^3
-// f16 blast (ms per step, n = 0 / n = 4): 4 planes 32.6 / 36.2, 5 planes
-// 31.0 / 35.0, 6 planes 32.6 / 36.5 (with the weight-table pass 2 6 planes
+// f16 blast (ms per step, n = 0 / n = 4): with the row quartic 5 planes
+// 28.1 / 33.4, 6 planes 28.0 / 32.0; before it 4 planes 32.6 / 36.2, 5
+// planes 31.0 / 35.0, 6 planes 32.6 / 36.5 (with the weight-table pass 2 6 planes
 // had been best: none 36.2 / 42.2, 4 35.2 / 41.3, 5 33.3 / 39.4, 6 33.0 /
 // 38.8, all 7 at 2 blocks per SM 43.9 / 46.9).  Float storage gained nothing
 // from 2 planes.  The second pass decodes the same stored bits, so the depth
 // does not change results.
 #ifndef LBM_Q343_STASH_HALF
-#define LBM_Q343_STASH_HALF 5
+#define LBM_Q343_STASH_HALF 6
 #endif
 #ifndef LBM_Q343_STASH_FLOAT
 #define LBM_Q343_STASH_FLOAT 0
@@ -95,8 +97,13 @@ __device__ __forceinline__ void q343_store(const Params<kQ343, ST> &p, int i, in
 // the plane factor w_c multiplies the plane sums once.  The collision
 // f* = (1 - omega) g + omega g^eq becomes d* = (1 - omega) d + (P - omega)
 // with P = omega rho g^eq / w, so no value is decoded to f or encoded back.
+// The equilibrium along each row is evaluated as a quartic in e_x (below),
+// 6 operations per pair of populations e_x = +-k instead of a full
+// polynomial evaluation for each.
 // Measured on the 384^3 f16 blast (ms per step, n = 0 / n = 4, 6 stash
-// planes): 33.7 / 40.1 with the weight table, 32.6 / 36.5 in this form; the
+// planes): 33.7 / 40.1 with the weight table, 32.6 / 36.5 in this form with
+// the equilibrium evaluated per population, 28.0 / 32.0 with the row
+// quartic (fewer registers: 8 bytes of spill instead of 176); the
 // same treatment of pass 1 (weighted deviation sums scaled by w_c per row)
 // took 35.4 / 45.0 alone and 36.5 / 40.2 with both (more registers, spills);
 // with 5 stash planes, 30.8 / 36.2 with both against 31.1 / 35.2 for pass 2
@@ -311,6 +318,15 @@ __device__ __forceinline__ void q343_collide_dev(const Params<kQ343, ST> &p, con
     const int self = o.self();
     float acc0 = 0.f, acc2 = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
     float P_c = 0.f, P_mx = 0.f, P_px = 0.f, P_my = 0.f, P_py = 0.f, P_mz = 0.f, P_pz = 0.f;
+    // Along a row (e_y, e_z fixed) c = C0 + e_x v and s = S0 + r^2 e_x^2, so
+    // P = A0(s) + A1(s) c + A2(s) c^2 + k6 c^3 + k24 c^4 is a quartic in e_x,
+    // b0 + b1 e_x + b2 e_x^2 + b3 e_x^3 + b4 e_x^4, whose coefficients follow
+    // from expanding it (b4 is the same for every row); the pairs e_x = +-k
+    // then share the even and odd parts.
+    const float v = rux, v2 = rux * rux;
+    const float k3k6 = 3.0f * k.k6, k4k24 = 4.0f * k.k24, k6k24 = 6.0f * k.k24;
+    const float a02x2 = 2.0f * k.a02, a21x2 = 2.0f * k.a21;
+    const float b4 = fmaf(k.a02, p.r2 * p.r2, fmaf(k.a21 * p.r2, v2, k.k24 * v2 * v2));
     float d_c = 0.f, d_mx = 0.f, d_px = 0.f, d_my = 0.f, d_py = 0.f, d_mz = 0.f, d_pz = 0.f;
     auto plane2 = [&](auto kept, int c) {
         constexpr bool KEPT = decltype(kept)::value;
@@ -325,13 +341,32 @@ __device__ __forceinline__ void q343_collide_dev(const Params<kQ343, ST> &p, con
             const float cyz = fmaf((float)ey, ruy, (float)ez * ruz);
             const float eyz2 = (float)(ey * ey) + ez2;
             const float syz = p.r2 * eyz2;
+            float Prow[7];
+            {
+                const float A0 = fmaf(syz, fmaf(syz, k.a02, k.a01), k.a00);
+                const float A1 = fmaf(syz, k.a11, k.a10);
+                const float A2 = fmaf(syz, k.a21, k.a20);
+                const float C0 = cyz;
+                const float b0 = fmaf(C0, fmaf(C0, fmaf(C0, fmaf(C0, k.k24, k.k6), A2), A1), A0);
+                const float b1 = v * fmaf(C0, fmaf(C0, fmaf(C0, k4k24, k3k6), A2 + A2), A1);
+                const float b2 = fmaf(p.r2, fmaf(C0, fmaf(C0, k.a21, k.a11), fmaf(a02x2, syz, k.a01)),
+                                      v2 * fmaf(C0, fmaf(C0, k6k24, k3k6), A2));
+                const float b3 = v * fmaf(p.r2, fmaf(C0, a21x2, k.a11), v2 * fmaf(C0, k4k24, k.k6));
+                Prow[3] = b0;
+#pragma unroll
+                for (int q = 1; q <= 3; ++q) {
+                    const float E = fmaf(b4, (float)(q * q * q * q), fmaf(b2, (float)(q * q), b0));
+                    const float O = (float)q * fmaf(b3, (float)(q * q), b1);
+                    Prow[3 + q] = E + O;
+                    Prow[3 - q] = E - O;
+                }
+            }
             float r0 = 0.f, r2 = 0.f, rx = 0.f;  // row sums (without w_c)
 #pragma unroll
             for (int a = 0; a < 7; ++a) {
                 const int ex = a - 3;
                 const int i = (c * 7 + b) * 7 + a;
-                const float cdot = fmaf((float)ex, rux, cyz);
-                const float P = eq_single(k, cdot, fmaf(p.r2, (float)(ex * ex), syz));
+                const float P = Prow[a];
                 r0 = fmaf(qw.w2[b * 7 + a], P, r0);
                 if (ex) {
                     r2 = fmaf(qw.w2x2[b * 7 + a], P, r2);
