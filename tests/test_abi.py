@@ -164,3 +164,54 @@ def test_node_reference_storage_sizes_and_limits(lbmlib):
         assert lbmlib.lbm_set_storage(h, 5) == -1  # unknown storage
     finally:
         lbmlib.lbm_destroy(h)
+
+
+def test_d3q343_weights_are_the_d1q7_tensor_product(lbmlib):
+    """The D3Q343 step forms each weight as (w_a w_b) w_c from the D1Q7
+    weights (the in-plane factor an immediate, the plane factor per plane),
+    so the library's D3Q343 set must be exactly that product with the index
+    i = (c * 7 + b) * 7 + a for e = (a - 3, b - 3, c - 3).  Host calls only."""
+    from paper_1606_06107_gb300 import lbm
+    r1, e1, w1 = lbm.lattice_info("D1Q7")
+    r3, e3, w3 = lbm.lattice_info("D3Q343")
+    assert r3 == r1
+    assert np.array_equal(e1[:, 0], np.arange(-3, 4))
+    for i in range(343):
+        a, b, c = i % 7, (i // 7) % 7, i // 49
+        assert tuple(e3[i]) == (a - 3, b - 3, c - 3)
+        assert abs(w3[i] - w1[a] * w1[b] * w1[c]) <= 1e-15 * w3[i]
+
+
+def test_row_quartic_expansion():
+    """The D3Q343 16-bit step evaluates the equilibrium polynomial of a row
+    (e_y, e_z fixed) as a quartic in e_x: with c = C0 + e_x v and s = S0 + r2
+    e_x^2, P = A0(s) + A1(s) c + A2(s) c^2 + k6 c^3 + k24 c^4 equals b0 + b1 e_x
+    + b2 e_x^2 + b3 e_x^3 + b4 e_x^4 with the coefficients written out in the
+    kernel's comments (A0 = a00 + a01 s + a02 s^2, A1 = a10 + a11 s, A2 = a20
+    + a21 s at s = S0).  Checked here in double precision on random
+    coefficients at the seven e_x of a row, and the pair form E +- O."""
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        a00, a01, a02, a10, a11, a20, a21, k6, k24 = rng.normal(size=9)
+        C0, S0, v = rng.normal(size=3)
+        r2 = 1.0 + rng.random()
+
+        def P(t):
+            s, c = S0 + r2 * t * t, C0 + v * t
+            return (a00 + a01 * s + a02 * s * s + (a10 + a11 * s) * c + (a20 + a21 * s) * c * c
+                    + k6 * c ** 3 + k24 * c ** 4)
+
+        A0, A1, A2 = a00 + a01 * S0 + a02 * S0 * S0, a10 + a11 * S0, a20 + a21 * S0
+        b0 = A0 + C0 * (A1 + C0 * (A2 + C0 * (k6 + C0 * k24)))
+        b1 = v * (A1 + C0 * (2 * A2 + C0 * (3 * k6 + 4 * k24 * C0)))
+        b2 = r2 * (a01 + 2 * a02 * S0 + a11 * C0 + a21 * C0 * C0) + v * v * (A2 + C0 * (3 * k6 + 6 * k24 * C0))
+        b3 = v * (r2 * (a11 + 2 * a21 * C0) + v * v * (k6 + 4 * k24 * C0))
+        b4 = a02 * r2 * r2 + a21 * r2 * v * v + k24 * v ** 4
+        for t in range(-3, 4):
+            want = P(t)
+            got = b0 + b1 * t + b2 * t * t + b3 * t ** 3 + b4 * t ** 4
+            assert abs(got - want) <= 1e-11 * (1 + abs(want)), (t, got, want)
+        for k in (1, 2, 3):
+            E, O = b0 + b2 * k * k + b4 * k ** 4, k * (b1 + b3 * k * k)
+            assert abs(E + O - P(k)) <= 1e-11 * (1 + abs(P(k)))
+            assert abs(E - O - P(-k)) <= 1e-11 * (1 + abs(P(-k)))
