@@ -158,7 +158,7 @@ def test_full_size_blast_config_sampled(orc):
                                         ((33, 2, 7), ("copy",) * 3, 4)])
 def test_one_step_per_population_16bit(orc, storage, shape, bc, n):
     """Every stored population after one step of the 16-bit kernel (ragged
-    128-node tiles, rows narrower than the pull reach, the 5-plane
+    128-node tiles, rows narrower than the pull reach, the 6-plane
     shared-memory stash) from a state the storage represents exactly, against the
     oracle's FP64 step from the same state: within one unit in the last
     place of the stored deviation plus float32 arithmetic (1e-5 of the
